@@ -1,0 +1,282 @@
+"""Pins of the FP64 oracle against closed forms, brute force, library routines
+and invariants (no GPU).  Each test names the mathematical fact it checks.
+
+A plausible mistake in the oracle fails at least one of these:
+  * wrong lens placement / masses      -> point-source closed form, symmetry
+  * dropped polynomial term / sign     -> numpy roots, Newton images, invariant
+  * bad validation tolerance / frame   -> image counts, Newton images
+  * wrong limb / sector coverage       -> Witt-Mao areas (incl. ring case), brute force
+  * quadrature weights / normalisation -> Witt-Mao, LD superposition integral
+  * derivative chain                   -> finite differences
+"""
+import numpy as np
+import pytest
+
+from paper_2510_02639_gb300 import inputs as I
+from tests import closed_forms as CF
+
+G = I.grid()
+
+
+def far_single(u0=0.0, rho=1e-3, u1=0.5, **kw):
+    # A binary whose companion is negligible (q = 1e-10) and far (s = 20):
+    # the single-lens limit, with the primary at the origin to 5e-10.
+    return I.binary(q=1e-10, s=20.0, u0=u0, alpha=0.0, t0=0.0, tE=1.0, rho=rho, u1=u1, **kw)
+
+
+# ---------------------------------------------------------------- point source
+@pytest.mark.parametrize("u", [0.01, 0.1, 0.5, 1.0, 3.0])
+def test_point_source_single_lens_limit(oracle_mod, u):
+    """(a) As q -> 0 the binary point-source magnification tends to
+    (u^2 + 2) / (u sqrt(u^2 + 4))."""
+    p = far_single()
+    eps, a = oracle_mod.lens(p)
+    A, n, _, st = oracle_mod.point_source(p, G, [a[0] + u])
+    assert st[0] == 0 and n[0] == 3
+    assert abs(A[0] / CF.single_lens_point(u) - 1) < 1e-7
+
+
+def test_signed_invariant_binary(oracle_mod):
+    """(c) For a binary lens and a source inside a caustic (five images) the
+    signed magnifications sum to 1 (Witt & Mao 1995)."""
+    rng = np.random.default_rng(7)
+    checked = 0
+    for q, s in [(0.1, 1.0), (1.0, 1.0), (0.5, 1.5), (1e-3, 1.0), (0.3, 0.7)]:
+        p = I.binary(q=q, s=s)
+        eps, a = oracle_mod.lens(p)
+        ws = rng.uniform(-0.25, 0.25, 60) + 1j * rng.uniform(-0.25, 0.25, 60)
+        A, n, z, st = oracle_mod.point_source(p, G, ws)
+        for i in range(len(ws)):
+            assert n[i] in (3, 5)
+            if n[i] != 5:
+                continue
+            zz = z[i, :5]
+            gam = np.array([np.sum(eps / (x - a) ** 2) for x in zz])
+            signed = np.sum(1.0 / (1.0 - np.abs(gam) ** 2))
+            assert abs(signed - 1.0) < 1e-9
+            checked += 1
+    assert checked >= 20
+
+
+@pytest.mark.parametrize("r", [30.0, 100.0, 300.0])
+def test_far_field(oracle_mod, r):
+    """(e) Far from the lenses A -> 1.  The positive image gives 1 + 1/u^4 and
+    the negative image beside each mass i (z ~ a_i - eps_i/conj(w)) gives
+    eps_i^2/u^4, so A - 1 -> (1 + sum_i eps_i^2)/u^4 + O(u^-5) (2/u^4 for one
+    lens)."""
+    for q in (0.3, 1e-3):
+        p = I.binary(q=q, s=1.0)
+        eps, a = oracle_mod.lens(p)
+        lead = (1.0 + np.sum(eps ** 2)) / r ** 4
+        for ph in (0.3, 1.7, 4.0):
+            w = r * np.exp(1j * ph)
+            A, n, _, _ = oracle_mod.point_source(p, G, [w])
+            assert n[0] == 3
+            assert abs((A[0] - 1.0) / lead - 1.0) < 4.0 / r
+
+
+# ---------------------------------------------------------------- polynomial
+@pytest.mark.parametrize("n_lens", [2, 3])
+def test_roots_match_numpy_companion(oracle_mod, n_lens):
+    """EA roots equal the eigenvalues of the companion matrix (numpy.roots) of
+    the oracle's own coefficients."""
+    rng = np.random.default_rng(3)
+    p = I.binary(q=2e-3, s=1.1) if n_lens == 2 else I.triple(q2=0.05, q3=0.02, s2=1.1, s3=0.9, psi=1.0)
+    for _ in range(10):
+        w = complex(rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3))
+        b = oracle_mod.poly(p, w, 0.0)
+        assert len(b) == (6 if n_lens == 2 else 11)
+        z, ok = oracle_mod.roots(p, w)
+        assert ok
+        ref = np.roots(b[::-1])
+        for zz in ref:
+            assert np.min(np.abs(z - zz)) < 1e-8 * max(1.0, abs(zz))
+
+
+@pytest.mark.parametrize("n_lens", [2, 3])
+def test_newton_images_are_roots_and_validated(oracle_mod, n_lens):
+    """Every solution of the lens equation found by plain 2-D Newton from many
+    starts is a root of the polynomial and is kept by the oracle's validation;
+    the oracle keeps no other root."""
+    rng = np.random.default_rng(11)
+    if n_lens == 2:
+        p = I.binary(q=0.2, s=1.0)
+    else:
+        p = I.triple(q2=0.1, q3=0.05, s2=1.0, s3=0.9, psi=1.2)
+    eps, a = oracle_mod.lens(p)
+    for _ in range(6):
+        w = complex(rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2))
+        sols = CF.newton_images(eps, a, w, n_start=1500)
+        A, n, z, st = oracle_mod.point_source(p, G, [w])
+        got = z[0, : n[0]]
+        assert len(sols) == n[0], (sols, got)
+        for s_ in sols:
+            assert np.min(np.abs(got - s_)) < 1e-9
+        allroots, _ = oracle_mod.roots(p, w)
+        b = oracle_mod.poly(p, w, 0.0)
+        for s_ in sols:
+            scale = np.sum(np.abs(b) * np.abs(s_) ** np.arange(len(b)))
+            assert abs(np.polyval(b[::-1], s_)) < 1e-11 * scale
+
+
+def test_small_mass_ratio_counts(oracle_mod):
+    """Validation in the lightest-lens frame keeps exactly 3 or 5 images down to
+    q = 1e-7 (the tiny image beside the planet is kept, spurious roots beside it
+    are rejected)."""
+    rng = np.random.default_rng(5)
+    for q in (1e-5, 1e-6, 1e-7):
+        for s in (0.6, 1.0, 1.8):
+            p = I.binary(q=q, s=s)
+            ws = rng.uniform(-0.3, 0.3, 40) + 1j * rng.uniform(-0.3, 0.3, 40)
+            A, n, z, st = oracle_mod.point_source(p, G, ws)
+            assert set(np.unique(n)) <= {3, 5}
+            assert np.all(st == 0)
+
+
+def test_triple_reduces_to_binary(oracle_mod):
+    """A triple lens whose third mass is negligible gives the binary result
+    (mass fractions eps2 = q2, eps1 = 1 - q2 <-> q = q2 / (1 - q2))."""
+    q2 = 0.01
+    tri = I.triple(q2=q2, q3=1e-10, s2=1.05, s3=4.0, psi=0.7, rho=1e-2, u0=0.05, alpha=0.4, tE=10.0, u1=0.6)
+    bi = I.binary(q=q2 / (1 - q2), s=1.05, rho=1e-2, u0=0.05, alpha=0.4, tE=10.0, u1=0.6)
+    t = np.linspace(-1.0, 1.0, 5)
+    ws = oracle_mod.source_centre(bi, t)
+    At, nt, _, _ = oracle_mod.point_source(tri, G, ws)
+    Ab, nb, _, _ = oracle_mod.point_source(bi, G, ws)
+    assert np.all(nt == nb + 1)  # plus the tiny image beside the far third mass
+    np.testing.assert_allclose(At, Ab, rtol=1e-8)
+    g = I.grid(n_r=48, n_theta=192)
+    Aft, _ = oracle_mod.magnification(tri, t, g)
+    Afb, _ = oracle_mod.magnification(bi, t, g)
+    np.testing.assert_allclose(Aft, Afb, rtol=2e-6)
+
+
+# ---------------------------------------------------------------- finite source
+@pytest.mark.parametrize("u_over_rho,rho", [(0.3, 0.05), (2.0, 0.05), (10.0, 0.01), (1.5, 1e-3)])
+def test_uniform_disk_witt_mao(oracle_mod, u_over_rho, rho):
+    """(b) Uniform disk, single-lens limit: the ICRS quadrature (uniform rule)
+    converges to the exact image area (Green's theorem; equivalent to the
+    Witt-Mao elliptic-integral form).  u < rho is the ring case (gap filling
+    across the ring's interior and the full-circle sector)."""
+    u = u_over_rho * rho
+    p = far_single(rho=rho, u1=0.0)
+    g = I.grid(n_r=512, n_theta=2048, uniform=1, n_limb=1000)
+    A, st = oracle_mod.magnification(p, [u], g)
+    ref = CF.single_lens_uniform_disk(u, rho)
+    # the radial midpoint sum converges as N_r^-1.5 where an image edge runs
+    # along a row (square-root end of the covered length); 1e-4 at N_r = 512
+    assert abs(A[0, 0] / ref - 1.0) < 1e-4, (A, ref)
+
+
+@pytest.mark.parametrize("u_over_rho,rho,u1", [(3.0, 0.05, 0.5), (0.5, 0.05, 0.6), (2.0, 5e-3, 0.3)])
+def test_limb_darkened_disk(oracle_mod, u_over_rho, rho, u1):
+    """(iii) Linear limb darkening, single-lens limit: the LD per-point rule
+    converges to the superposition-of-uniform-disks integral."""
+    u = u_over_rho * rho
+    p = far_single(rho=rho, u1=u1)
+    g = I.grid(n_r=512, n_theta=2048, n_limb=1000)
+    A, st = oracle_mod.magnification(p, [u], g)
+    ref = CF.single_lens_ld_disk(u, rho, u1)
+    assert abs(A[0, 0] / ref - 1.0) < 1e-4, (A, ref)
+
+
+@pytest.mark.parametrize("case", [
+    dict(q=0.2, s=1.0, w=0.02 + 0.01j, uniform=1, u1=0.0),
+    dict(q=0.05, s=1.3, w=0.3 - 0.05j, uniform=0, u1=0.5),
+    dict(q=1.0, s=0.8, w=0.05 + 0.04j, uniform=0, u1=0.7),
+])
+def test_brute_force_binary(oracle_mod, case):
+    """(d) Binary lens, rho = 0.05: the oracle agrees with Cartesian inverse-ray
+    shooting (independent of the polar sectors) to the brute force's pixel error."""
+    rho = 0.05
+    w = case["w"]
+    p = I.binary(q=case["q"], s=case["s"], rho=rho, u1=case["u1"], t0=0.0, tE=1.0, u0=w.imag, alpha=0.0)
+    g = I.grid(n_r=200, n_theta=800, uniform=case["uniform"])
+    A, st = oracle_mod.magnification(p, [w.real], g)
+    eps, a = oracle_mod.lens(p)
+    ref = CF.brute_force_magnification(eps, a, w, rho, u1=case["u1"], uniform=bool(case["uniform"]),
+                                       refine=120)
+    assert abs(A[0, 0] / ref - 1.0) < 2e-3, (A, ref)
+
+
+def test_mirror_symmetry(oracle_mod):
+    """(vi) Both lenses lie on the real axis, so the map commutes with complex
+    conjugation: (alpha, u0) -> (-alpha, -u0) conjugates every source position
+    and leaves the magnification unchanged."""
+    p = I.binary(q=1e-3, s=1.0, rho=1e-3, u1=0.5, u0=0.01, alpha=0.5)
+    pm = dict(p, alpha=-0.5, u0=-0.01)
+    t = np.linspace(-0.5, 0.5, 21)
+    A, _ = oracle_mod.magnification(p, t, G)
+    Am, _ = oracle_mod.magnification(pm, t, G)
+    np.testing.assert_allclose(A, Am, rtol=1e-11)
+
+
+def test_centred_ring_radial_rule(oracle_mod):
+    """(v) Source centred on a single lens: the image is an annulus whose edges
+    run along the rows, the angular rule is exact and the whole error is the
+    radial midpoint sum of a step function, |error| <= 2 dr / (r_out - r_in)
+    relative; A -> sqrt(1 + 4/rho^2) as N_r grows."""
+    rho = 0.01
+    p = far_single(rho=rho, u1=0.0)
+    ref = np.sqrt(1.0 + 4.0 / rho ** 2)
+    for nr in (64, 512):
+        g = I.grid(n_r=nr, n_theta=256, uniform=1)
+        A, st = oracle_mod.magnification(p, [0.0], g)
+        boxes, _ = oracle_mod.sectors(p, 0.0, g)
+        dr = (boxes[0, 1] - boxes[0, 0]) / nr
+        assert boxes[0, 4] == 1.0  # full-circle sector
+        assert abs(A[0, 0] / ref - 1.0) <= 2.0 * dr / rho
+
+
+def test_sectors_cover_all_images(oracle_mod):
+    """Every ray that lands inside the source (Cartesian brute force) lies in one
+    of the oracle's sectors, and the sectors do not overlap."""
+    p = I.binary(q=1e-3, s=1.0, rho=1e-3, u1=0.5, u0=0.01, alpha=0.5)
+    eps, a = oracle_mod.lens(p)
+    for t in (-0.3, -0.05, 0.0, 0.12):
+        boxes, st = oracle_mod.sectors(p, t, G)
+        wc = oracle_mod.source_centre(p, t)[0]
+        # dense rays around the Einstein ring where the images are
+        r = np.linspace(0.9, 1.1, 1201)
+        th = np.linspace(-np.pi, np.pi, 6001, endpoint=False)
+        R, TH = np.meshgrid(r, th, indexing="ij")
+        z = R * np.exp(1j * TH)
+        inside = np.abs(CF.lens_map(eps, a, z) - wc) < p["rho"]
+        cov = np.zeros_like(inside)
+        for (rlo, rhi, tlo, wd, per) in boxes:
+            inr = (R >= rlo) & (R <= rhi)
+            d = np.mod(TH - tlo, 2 * np.pi)
+            inth = np.ones_like(inr) if per else d <= wd
+            assert not np.any(cov & inr & inth & inside)
+            cov |= inr & inth
+        assert np.all(cov[inside])
+
+
+def test_forward_mode_matches_fd(oracle_mod):
+    """(vii) The oracle's 8-direction forward-mode derivative equals central
+    finite differences of its own primal.  The primal is piecewise smooth
+    (inclusion flags jump, and the extremal limb point behind a sector bound
+    can change), so a pair (epoch, parameter) is compared only where two step
+    sizes give the same difference quotient; nearly all pairs qualify."""
+    p = I.binary(q=0.05, s=1.2, rho=0.02, u1=0.5, u0=0.1, alpha=0.8, tE=20.0, t0=0.0)
+    g = I.grid(n_r=48, n_theta=160, n_limb=200)
+    t = np.array([-3.0, -1.0, 0.4, 1.3, 2.5, 6.0])
+    A, dA, _ = oracle_mod.magnification_fwd(p, t, g)
+    keys = ["t0", "tE", "u0", "alpha", "s", "q", "rho", "u1"]
+    rel = {"tE", "s", "q", "rho"}
+    compared = agreed = 0
+    for i, k in enumerate(keys):
+        fd = []
+        for h0 in (1e-7, 2e-7):
+            h = h0 * p[k] if k in rel else h0
+            Ap, _ = oracle_mod.magnification(dict(p, **{k: p[k] + h}), t, g)
+            Am, _ = oracle_mod.magnification(dict(p, **{k: p[k] - h}), t, g)
+            fd.append((Ap[0] - Am[0]) / (2 * h))
+        for e in range(len(t)):
+            scale = max(1.0, abs(fd[0][e]))
+            if abs(fd[0][e] - fd[1][e]) > 2e-5 * scale:
+                continue
+            compared += 1
+            agreed += abs(dA[0, e, i] - fd[0][e]) <= 5e-5 * scale
+    assert compared >= 40
+    assert agreed == compared
