@@ -1,0 +1,167 @@
+/*
+ * icrs.h - C ABI of the GB300 image-centred ray shooting (ICRS) library.
+ *
+ * The library computes microlensing magnifications of a limb-darkened
+ * extended source by a binary or triple point-mass lens with the ICRS method
+ * of Miyazaki & Kawahara (arXiv:2510.02639, "microJAX"):
+ *   - point-source images from the roots of the complex lens polynomial
+ *     (Sec. 2.1, Eqs. lens_eq, amp_point, detJ, lens_eq_z; Ehrlich-Aberth
+ *     iteration, Sec. 3.1),
+ *   - image-centred polar sectors built from binned image-limb points
+ *     (Sec. 3.2),
+ *   - a fixed N_r x N_theta polar grid per sector whose rays are mapped
+ *     through the lens equation, with the uniform / linear limb-darkening
+ *     quadrature of Appendix A (Sec. 3.3).
+ *
+ * Conventions used by every entry point
+ *   - All array arguments are DEVICE pointers owned by the caller (for
+ *     example torch.Tensor.data_ptr()), contiguous, row-major.  Structs passed
+ *     by pointer as "host" are read on the host before the call returns.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it and the entry points return without synchronising it
+ *     (except when icrs_grid.n_lens = 0, see there).
+ *   - The library allocates no device memory in these entry points.
+ *   - Return value: ICRS_OK or an error code below; on error nothing has been
+ *     enqueued (argument errors) or the CUDA error is reported (ICRS_ECUDA).
+ *   - Kernels never trap: per-item problems are reported in `status` words.
+ */
+#ifndef ICRS_H
+#define ICRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define ICRS_OK 0
+#define ICRS_EINVAL 1        /* bad argument: NaN, q <= 0, rho <= 0, grid out of range */
+#define ICRS_ECUDA 2         /* a CUDA runtime call failed */
+#define ICRS_ETIMEOUT 3      /* a bounded device wait expired */
+#define ICRS_EUNSUPPORTED 4  /* valid request this build cannot serve (e.g. shared memory) */
+
+/* Per-item status bits (OR-ed). */
+#define ICRS_ST_NONCONV 1u   /* a root iteration hit its iteration cap */
+#define ICRS_ST_IMGCOUNT 2u  /* illegal image count (binary: 3 or 5; triple: 4,6,8,10) */
+#define ICRS_ST_SECTCAP 4u   /* more sectors than N_deg: the closest ones were merged */
+#define ICRS_ST_EDGE 8u      /* an inside ray touched a non-periodic grid edge */
+#define ICRS_ST_NAN 16u      /* non-finite result */
+#define ICRS_ST_OVERFLOW 32u /* an on-chip table overflowed; a decision was taken in FP32 */
+/* icrs_magnification also stores the number of sectors integrated for the
+ * epoch in bits 8..15 of its status word. */
+#define ICRS_ST_NSECT(st) (((st) >> 8) & 0xffu)
+
+/*
+ * Model parameters of one light curve (one "parameter set").
+ *   t0, tE      time of closest approach to the origin, Einstein time (days)
+ *   u0, alpha   impact parameter and trajectory angle to the binary axis:
+ *               w_c(t) = tau (cos a, sin a) + u0 (-sin a, cos a),
+ *               tau = (t - t0) / tE                       (Sec. 3.5, Fig. 3)
+ *   rho         source radius in Einstein radii (> 0)
+ *   u1          linear limb-darkening coefficient in [0, 1) (Appendix A.2)
+ *   n_lens      2 (binary) or 3 (triple)
+ *   binary:     s = separation, q = m2/m1 (> 0); masses eps1 = 1/(1+q),
+ *               eps2 = q/(1+q); lenses on the real axis with the primary at
+ *               -q s/(1+q), origin at the centre of mass (Eq. lens_eq).
+ *   triple:     q2, q3 = mass fractions of lenses 2 and 3, eps1 = 1 - q2 - q3;
+ *               lenses 1, 2 on the real axis s2 apart with the origin at their
+ *               barycentre; lens 3 at (midpoint of 1,2) + s3 e^{i psi} (Fig. 3).
+ */
+typedef struct {
+  double t0, tE, u0, alpha, rho, u1;
+  int32_t n_lens;
+  int32_t reserved;
+  double s, q;
+  double q2, q3, s2, s3, psi;
+} icrs_params;
+
+/*
+ * Discretisation (host struct).
+ *   n_r, n_theta   polar grid per sector (Sec. 3.3): 1..4096, 8..8192
+ *   n_limb         source-limb points (Sec. 3.2): 16..1024
+ *   n_bins_r       radial bins per angular interval: 2..32
+ *   n_bins_theta   angular bins over [-pi, pi): 2..64
+ *   max_iter       cap on root iterations
+ *   uniform        1: uniform source (Appendix A.1 rule), 0: linear LD
+ *   delta_c        threshold of the LD correction f(delta) (Appendix A.2), > 0
+ *   margin         sector widening, fraction of the extent per side (>= 0)
+ *   img_tol        lens-equation residual below which a root is an image
+ *   n_lens         see the field comment
+ */
+typedef struct {
+  int32_t n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter, uniform;
+  int32_t n_lens;  /* lens count shared by every set of the call (2 or 3); 0 = read it
+                      from the first set on the device, which synchronises `stream` */
+  double delta_c, margin, img_tol;
+} icrs_grid;
+
+/* Fills `g` with the library defaults (64 x 256 grid, 500 limb points, 32 x 64
+ * bins, delta_c = 0.02, margin = 0.05, img_tol = 1e-3, linear LD, n_lens = 2). */
+void icrs_grid_default(icrs_grid* g);
+
+/*
+ * Point-source magnification A = sum_j 1/|det J(z_j)| (Eqs. amp_point, detJ).
+ *   p       [S] device icrs_params
+ *   w       [S][n][2] device double: source positions (x, y) per set
+ *   A       [S][n] device double (out)
+ *   images  [S][n][N_deg][2] device double or NULL (out): image positions,
+ *           first n_img[i] entries valid; N_deg = 5 (binary) or 10 (triple)
+ *   n_img   [S][n] device int32 or NULL (out)
+ *   status  [S][n] device uint32 or NULL (out): ICRS_ST_* bits
+ * Images are roots of the lens polynomial whose lens-equation residual is
+ * below img_tol (FP32 Ehrlich-Aberth, FP64 polish and validation).
+ */
+int icrs_point_source(const icrs_params* p, int S, const double* w, int n,
+                      const icrs_grid* g, double* A, double* images,
+                      int32_t* n_img, uint32_t* status, void* stream);
+
+/*
+ * Finite-source magnification of S light curves x E epochs (Sec. 3,
+ * Appendix A).
+ *   p       [S] device icrs_params (all sets must share n_lens)
+ *   t       [S][E] device double: epoch times
+ *   g       host icrs_grid
+ *   A       [S][E] device double (out)
+ *   status  [S][E] device uint32 or NULL (out)
+ * One persistent CUDA kernel runs the whole per-epoch path: limb roots,
+ * sectors, rays and the brightness reduction.  Errors: ICRS_EINVAL for bad
+ * sizes or grid, ICRS_EUNSUPPORTED if the grid needs more shared memory than
+ * an SM has, ICRS_ECUDA on launch failure.
+ */
+int icrs_magnification(const icrs_params* p, int S, const double* t, int E,
+                       const icrs_grid* g, double* A, uint32_t* status,
+                       void* stream);
+
+/*
+ * icrs_magnification plus per-epoch diagnostics (for tests and profiling):
+ *   sectors   [S][E][10][5] device double or NULL: the sectors integrated,
+ *             (r_lo, r_hi, theta_lo, width, periodic), unused rows zero
+ *   counters  [S][E][16] device int32 or NULL: [0] image-limb points polished
+ *             in FP64, [1] roots validated in FP64, [2] rays recomputed in
+ *             FP64, [3] boundary crossings recomputed in FP64, [4..12] SM
+ *             clock cycles spent in the kernel's phases (roots, FP64
+ *             validation, theta bins, theta runs and r ranges, r bins, gap
+ *             probes, cell extremes, sector merging, rays), [13..15] zero
+ *   points    [S][E][N_limb][N_deg][4] device float or NULL: image-limb points
+ *             (r, theta, flags, FP32 error bound) after root validation
+ * Same semantics and errors as icrs_magnification; the diagnostics add shared
+ * memory atomics on the FP64 fallback paths and clock reads.
+ */
+int icrs_magnification_diag(const icrs_params* p, int S, const double* t, int E,
+                            const icrs_grid* g, double* A, uint32_t* status,
+                            double* sectors, int32_t* counters, float* points,
+                            void* stream);
+
+/* Message for a return code (static string). */
+const char* icrs_strerror(int code);
+
+/* Version of the library ABI (increments on incompatible changes). */
+int icrs_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ICRS_H */

@@ -63,6 +63,8 @@ def lib():
         L.orc_sectors.argtypes = [dp, ctypes.c_double, dp, dp, ctypes.c_int, up]
         L.orc_sectors.restype = ctypes.c_int
         L.orc_magnification.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, dp, dp, up]
+        L.orc_limb_points.argtypes = [dp, ctypes.c_double, dp, dp]
+        L.orc_limb_points.restype = ctypes.c_int
         L.orc_magnification_fwd.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, dp, dp, dp, up]
         _lib = L
     return _lib
@@ -192,3 +194,13 @@ def magnification_fwd(params, t, grid: dict):
                                 dA.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                 st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
     return A, dA, st
+
+
+def limb_points(p: dict, t: float, grid: dict) -> np.ndarray:
+    """Image-limb points of one epoch: [N_limb, N_deg, 3] = (r, theta, valid)."""
+    prm, pp = _d(param_vector(p))
+    g, gp = _d(grid_vector(grid))
+    nd = 5 if int(p.get("n_lens", 2)) == 2 else 10
+    out = np.zeros(int(grid["n_limb"]) * nd * 3)
+    lib().orc_limb_points(pp, float(t), gp, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out.reshape(int(grid["n_limb"]), nd, 3)

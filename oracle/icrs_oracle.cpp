@@ -997,6 +997,30 @@ int orc_sectors(const double* prm, double t, const double* grid, double* out, in
   return n;
 }
 
+// Image-limb points of one epoch: out[(k * ndeg + j) * 3 + {r, theta, valid}]
+// for every root j of limb point k (Sec. 3.2).  Returns ndeg.
+int orc_limb_points(const double* prm, double t, const double* grid, double* out) {
+  Grid G = grid_from(grid);
+  Par<double> P = par_from<double>(prm, false);
+  Lens<double> L = make_lens<double>(prm, P.s, P.q);
+  C wc = source_centre(P, t);
+  int ndeg = L.n * L.n + 1;
+  for (int k = 0; k < G.n_limb; ++k) {
+    double ph = 2.0 * PI * k / G.n_limb;
+    C w = wc + C(P.rho * std::cos(ph), P.rho * std::sin(ph));
+    Root R[16];
+    lens_roots(L, w, G.max_iter, R);
+    for (int j = 0; j < ndeg; ++j) {
+      C z = L.a[R[j].j] + R[j].x;
+      double* o = out + ((size_t)k * ndeg + j) * 3;
+      o[0] = cabs(z);
+      o[1] = std::atan2(z.im, z.re);
+      o[2] = is_image(L, R[j], w, G.img_tol) ? 1.0 : 0.0;
+    }
+  }
+  return ndeg;
+}
+
 // Finite-source magnification for S parameter sets x E epochs.
 // prm[S][14], t[S][E], A[S][E], status[S][E] (optional).
 void orc_magnification(const double* prm, int S, const double* t, int E, const double* grid,

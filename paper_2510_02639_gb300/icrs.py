@@ -1,0 +1,173 @@
+"""Python binding of the ICRS C ABI (include/icrs.h).
+
+Argument marshalling only: every step of the magnification path runs in the
+CUDA library ``libicrs.so``.  PyTorch supplies device memory and the current
+stream.  If the library is missing the import of this module raises; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libicrs.so")
+
+ICRS_OK, ICRS_EINVAL, ICRS_ECUDA, ICRS_ETIMEOUT, ICRS_EUNSUPPORTED = 0, 1, 2, 3, 4
+ST_NONCONV, ST_IMGCOUNT, ST_SECTCAP, ST_EDGE, ST_NAN, ST_OVERFLOW = 1, 2, 4, 8, 16, 32
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTED = ("icrs_grid_default", "icrs_point_source", "icrs_magnification",
+            "icrs_magnification_diag", "icrs_strerror", "icrs_abi_version")
+
+
+class IcrsParams(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_double), ("tE", ctypes.c_double), ("u0", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("rho", ctypes.c_double), ("u1", ctypes.c_double),
+                ("n_lens", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("s", ctypes.c_double), ("q", ctypes.c_double),
+                ("q2", ctypes.c_double), ("q3", ctypes.c_double), ("s2", ctypes.c_double),
+                ("s3", ctypes.c_double), ("psi", ctypes.c_double)]
+
+
+class IcrsGrid(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32), ("n_limb", ctypes.c_int32),
+                ("n_bins_r", ctypes.c_int32), ("n_bins_theta", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("uniform", ctypes.c_int32), ("n_lens", ctypes.c_int32),
+                ("delta_c", ctypes.c_double), ("margin", ctypes.c_double), ("img_tol", ctypes.c_double)]
+
+
+PARAMS_DTYPE = np.dtype([("t0", "<f8"), ("tE", "<f8"), ("u0", "<f8"), ("alpha", "<f8"),
+                         ("rho", "<f8"), ("u1", "<f8"), ("n_lens", "<i4"), ("reserved", "<i4"),
+                         ("s", "<f8"), ("q", "<f8"), ("q2", "<f8"), ("q3", "<f8"),
+                         ("s2", "<f8"), ("s3", "<f8"), ("psi", "<f8")])
+assert PARAMS_DTYPE.itemsize == ctypes.sizeof(IcrsParams)
+
+
+class IcrsError(RuntimeError):
+    pass
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library {LIB_PATH} is missing: run __graft_entry__.build() "
+                          f"(or python -m paper_2510_02639_gb300.build)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    L.icrs_grid_default.argtypes = [ctypes.POINTER(IcrsGrid)]
+    L.icrs_grid_default.restype = None
+    L.icrs_point_source.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid),
+                                    vp, vp, vp, vp, vp]
+    L.icrs_point_source.restype = ctypes.c_int
+    L.icrs_magnification.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid),
+                                     vp, vp, vp]
+    L.icrs_magnification.restype = ctypes.c_int
+    L.icrs_magnification_diag.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid),
+                                          vp, vp, vp, vp, vp, vp]
+    L.icrs_magnification_diag.restype = ctypes.c_int
+    L.icrs_strerror.argtypes = [ctypes.c_int]
+    L.icrs_strerror.restype = ctypes.c_char_p
+    L.icrs_abi_version.restype = ctypes.c_int
+    return L
+
+
+lib = _load()
+
+
+def check(rc: int):
+    if rc != ICRS_OK:
+        raise IcrsError(f"icrs error {rc}: {lib.icrs_strerror(rc).decode()}")
+
+
+def make_grid(**kw) -> IcrsGrid:
+    g = IcrsGrid()
+    lib.icrs_grid_default(ctypes.byref(g))
+    for k, v in kw.items():
+        setattr(g, k, v)
+    return g
+
+
+def params_array(params) -> np.ndarray:
+    """Pack a list of parameter dicts into the C struct layout."""
+    a = np.zeros(len(params), dtype=PARAMS_DTYPE)
+    for i, p in enumerate(params):
+        for k in PARAMS_DTYPE.names:
+            if k == "reserved":
+                continue
+            a[i][k] = p.get(k, 0)
+    return a
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(torch, stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def params_to_device(params, device="cuda"):
+    import torch
+    a = params_array(params)
+    return torch.from_numpy(a.view(np.uint8).copy()).to(device)
+
+
+def magnification(params_dev, t, grid: IcrsGrid, out=None, status=None, stream=None):
+    """Finite-source magnification.  params_dev: uint8 device tensor holding S
+    icrs_params structs; t: [S, E] float64 device tensor.  Returns (A, status)."""
+    import torch
+    S = params_dev.numel() // PARAMS_DTYPE.itemsize
+    assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    E = t.shape[-1] if t.dim() > 0 else 0
+    if out is None:
+        out = torch.empty((S, E), dtype=torch.float64, device=t.device)
+    if status is None:
+        status = torch.empty((S, E), dtype=torch.int32, device=t.device)
+    check(lib.icrs_magnification(_ptr(params_dev), S, _ptr(t), E, ctypes.byref(grid),
+                                 _ptr(out), _ptr(status), _stream(torch, stream)))
+    return out, status
+
+
+def magnification_diag(params_dev, t, grid: IcrsGrid, points=False, stream=None):
+    """As magnification(), plus sectors [S, E, 10, 5], counters [S, E, 16] and
+    optionally the image-limb points [S, E, N_limb * N_deg, 4] per epoch."""
+    import torch
+    S = params_dev.numel() // PARAMS_DTYPE.itemsize
+    E = t.shape[-1]
+    out = torch.empty((S, E), dtype=torch.float64, device=t.device)
+    status = torch.empty((S, E), dtype=torch.int32, device=t.device)
+    sect = torch.empty((S, E, 10, 5), dtype=torch.float64, device=t.device)
+    cnt = torch.empty((S, E, 16), dtype=torch.int32, device=t.device)
+    nd = 5 if grid.n_lens == 2 else 10
+    pts = torch.empty((S, E, grid.n_limb * nd, 4), dtype=torch.float32, device=t.device) if points else None
+    check(lib.icrs_magnification_diag(_ptr(params_dev), S, _ptr(t), E, ctypes.byref(grid), _ptr(out),
+                                      _ptr(status), _ptr(sect), _ptr(cnt), _ptr(pts), _stream(torch, stream)))
+    return out, status, sect, cnt, pts
+
+
+def point_source(params_dev, w, grid: IcrsGrid, n_lens=2, stream=None):
+    """Point-source magnification at positions w: [S, n, 2] float64 device.
+    Returns (A [S, n], images [S, n, N_deg, 2], n_img [S, n], status [S, n])."""
+    import torch
+    S = params_dev.numel() // PARAMS_DTYPE.itemsize
+    n = w.shape[1]
+    nd = 5 if n_lens == 2 else 10
+    A = torch.empty((S, n), dtype=torch.float64, device=w.device)
+    imgs = torch.empty((S, n, nd, 2), dtype=torch.float64, device=w.device)
+    nimg = torch.empty((S, n), dtype=torch.int32, device=w.device)
+    st = torch.empty((S, n), dtype=torch.int32, device=w.device)
+    check(lib.icrs_point_source(_ptr(params_dev), S, _ptr(w), n, ctypes.byref(grid), _ptr(A),
+                                _ptr(imgs), _ptr(nimg), _ptr(st), _stream(torch, stream)))
+    return A, imgs, nimg, st
+
+
+def grid_from_dict(d: dict, n_lens: int = 2) -> IcrsGrid:
+    return make_grid(n_r=int(d["n_r"]), n_theta=int(d["n_theta"]), n_limb=int(d["n_limb"]),
+                     n_bins_r=int(d["n_bins_r"]), n_bins_theta=int(d["n_bins_theta"]),
+                     max_iter=int(d["max_iter"]), uniform=int(d["uniform"]), n_lens=int(n_lens),
+                     delta_c=float(d["delta_c"]), margin=float(d["margin"]),
+                     img_tol=float(d["img_tol"]))
