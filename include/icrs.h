@@ -143,7 +143,8 @@ int icrs_magnification(const icrs_params* p, int S, const double* t, int E,
  *             FP64, [3] boundary crossings recomputed in FP64, [4..12] SM
  *             clock cycles spent in the kernel's phases (roots, FP64
  *             validation, theta bins, theta runs and r ranges, r bins, gap
- *             probes, cell extremes, sector merging, rays), [13..15] zero
+ *             probes, cell extremes, sector merging, rays), [13..15] running
+ *             count of [0] after the theta-bin, r-range and r-bin phases
  *   points    [S][E][N_limb][N_deg][4] device float or NULL: image-limb points
  *             (r, theta, flags, FP32 error bound) after root validation
  * Same semantics and errors as icrs_magnification; the diagnostics add shared

@@ -37,7 +37,7 @@ namespace icrs {
 constexpr int NT = 512;          // threads per block (one block per SM)
 constexpr int NW = NT / 32;      // warps per block
 constexpr int QMAX = 2048;       // work queue
-constexpr int PMAX = 1024;       // FP64-polished image-limb points per epoch
+constexpr int PMAX_MIN = 512;    // FP64-polished image-limb points per epoch (at least)
 constexpr int MAXT = 32;         // theta runs (<= n_bins_theta / 2)
 constexpr int MAXRB = 32;        // r bins per theta run
 constexpr int MAXCELL = 96;      // (theta run, r run) cells
@@ -277,7 +277,7 @@ template <int NL>
 __global__ void __launch_bounds__(NT, 1)
 mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ T_, int E,
            icrs_grid g, int tiles_per_block, double* __restrict__ A_out, uint32_t* __restrict__ st_out,
-           double* __restrict__ diag_sect, int32_t* __restrict__ diag_cnt, float* __restrict__ diag_pts) {
+           double* __restrict__ diag_sect, int32_t* __restrict__ diag_cnt, float* __restrict__ diag_pts, int PMAX) {
   constexpr int N = NL * NL + 1;
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Shared sh;
@@ -293,6 +293,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   // error bound, flags, bins, index into the FP64 table
   cf* phi = (cf*)p;              p += sizeof(cf) * NP;
   float* r32 = (float*)p;        p += sizeof(float) * NP;
+  float* rl32 = (float*)p;       p += sizeof(float) * NP;   // r = r32 + rl32 (double-float)
   float* t32 = (float*)p;        p += sizeof(float) * NP;
   float* e32 = (float*)p;        p += sizeof(float) * NP;
   short* pidx = (short*)p;       p += sizeof(short) * ((NP + 7) & ~7);
@@ -306,7 +307,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   cf* tab = (cf*)p;              p += sizeof(cf) * g.n_theta;
   const int seg = g.n_theta < 1024 ? g.n_theta : 1024;
   float* rowbuf = (float*)p;     p += sizeof(float) * NW * (seg + 4);
-  cdf* ulimb = (cdf*)p;          // e^{2 pi i k / N_limb} as double-float
+  cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
+  int* wqueue = (int*)p;         // NW x 64 boundary points of the current row
 
   if (tid == 0) { sh.cur_set = -1; sh.warm = 0; }
   for (int k = tid; k < K; k += NT) {
@@ -539,10 +541,17 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         df zx = df_add(px, sh.adf_ll[0]);
         df zy = df_add(py, sh.adf_ll[1]);
         float zxf = zx.hi + zx.lo, zyf = zy.hi + zy.lo;
-        float rr = sqrtf(zxf * zxf + zyf * zyf);
+        // r = |z| as a double-float: r^2 in double-float, then one Newton
+        // correction of the float square root
+        df r2 = df_add(df_mul(zx, zx), df_mul(zy, zy));
+        float rr = sqrtf(r2.hi);
+        df rsq = two_prod(rr, rr);
+        float rlo = ((r2.hi - rsq.hi) - rsq.lo + r2.lo) / (2.0f * rr);
         float th = atan2f(zyf, zxf);
+        // error bound of the double-float r after the step: second-order Newton
+        // term plus the double-float residual's rounding
         float ee = 4.0f * sqrtf(abs2(g3)) * adz2 * jinv + jinv * 1e-12f * (1.0f + noise / (16.0f * EPS32)) +
-                   2.0f * EPS32 * rr;
+                   1e-12f * rr;
         if (!(rr == rr) || !(th == th) || !(ee == ee) || isinf(ee)) {
           meta[pslot] = M_UNSURE;
           phi[pslot] = mk(px.hi, py.hi);
@@ -551,6 +560,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         meta[pslot] = M_VALID;
         phi[pslot] = mk(px.hi, py.hi);
         r32[pslot] = rr;
+        rl32[pslot] = rlo;
         t32[pslot] = th;
         e32[pslot] = ee;
       }
@@ -575,8 +585,9 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         uint8_t m = 0;
         if (ok) {
           int pi = atomicAdd(&sh.pn, 1);
-          if (pi < PMAX) { pr[pi] = r; pt[pi] = th; pidx[ps] = (short)pi; m = M_VALID | M_EXACT; r32[ps] = (float)r; t32[ps] = (float)th; e32[ps] = 0.f; }
-          else { m = M_VALID; atomicOr(&sh.status, ICRS_ST_OVERFLOW); r32[ps] = (float)r; t32[ps] = (float)th; }
+          float rh = (float)r;
+          if (pi < PMAX) { pr[pi] = r; pt[pi] = th; pidx[ps] = (short)pi; m = M_VALID | M_EXACT; r32[ps] = rh; rl32[ps] = (float)(r - (double)rh); t32[ps] = (float)th; e32[ps] = 0.f; }
+          else { m = M_VALID; atomicOr(&sh.status, ICRS_ST_OVERFLOW); r32[ps] = rh; rl32[ps] = (float)(r - (double)rh); t32[ps] = (float)th; e32[ps] = 1e-12f; }
         }
         meta[ps] = m;
       }
@@ -608,7 +619,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         int pi = atomicAdd(&sh.pn, 1);
         if (pi < PMAX) {
           pr[pi] = r; pt[pi] = th; pidx[ps] = (short)pi;
-          r32[ps] = (float)r; t32[ps] = (float)th; e32[ps] = 0.f;
+          float rh = (float)r;
+          r32[ps] = rh; rl32[ps] = (float)(r - (double)rh); t32[ps] = (float)th; e32[ps] = 0.f;
           meta[ps] |= M_EXACT;
         } else {
           atomicOr(&sh.status, ICRS_ST_OVERFLOW);
@@ -618,7 +630,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       if (tid == 0) sh.qn = 0;
       __syncthreads();
     };
-    auto rv = [&](int ps) -> double { return (meta[ps] & M_EXACT) ? pr[pidx[ps]] : (double)r32[ps]; };
+    // r of a slot: FP64 if polished, else the double-float (r32 + rl32)
+    auto rv = [&](int ps) -> double { return (meta[ps] & M_EXACT) ? pr[pidx[ps]] : (double)r32[ps] + (double)rl32[ps]; };
     auto tv = [&](int ps) -> double { return (meta[ps] & M_EXACT) ? pt[pidx[ps]] : (double)t32[ps]; };
 
     if (diag_pts) {
@@ -655,6 +668,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     __syncthreads();
 
     if (diag_cnt && tid == 0) { long long c_ = clock64(); sh.cnt[6] = (int)min(c_ - sh.clk0, 2000000000LL); sh.clk0 = c_; }
+    if (diag_cnt && tid == 0) sh.cnt[13] = sh.cnt[0];
     // ------------------------------------------------ 3. theta runs (cyclic)
     if (tid == 0) {
       unsigned long long occ = sh.tocc;
@@ -710,7 +724,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       // an image smaller than tiny contributes below the parity tolerance:
       // its decisions stay in FP32
       bool is_tiny = fkey_inv(sh.t_rhi_l[T]) - fkey_inv(sh.t_rlo_u[T]) < tiny;
-      if (cand) { meta[ps] |= M_CAND; if (!(meta[ps] & M_EXACT) && !is_tiny) q_push(sh, queue, ps); }
+      // the double-float r (error e32) is exact enough unless e32 is large
+      if (cand) { meta[ps] |= M_CAND; if (!(meta[ps] & M_EXACT) && !is_tiny && !(e32[ps] <= 1e-11f)) q_push(sh, queue, ps); }
     }
     run_polish();
     for (int ps = tid; ps < NP; ps += NT) {
@@ -730,17 +745,30 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     __syncthreads();
 
     if (diag_cnt && tid == 0) { long long c_ = clock64(); sh.cnt[7] = (int)min(c_ - sh.clk0, 2000000000LL); sh.clk0 = c_; }
+    if (diag_cnt && tid == 0) sh.cnt[14] = sh.cnt[0];
     // ------------------------------------------------ 5. r bins per theta run
+    // Bin of r within its angular interval, floor((r - r_lo) / h_r): in FP32
+    // from the double-float r where the bin edge is farther than the FP32
+    // error, else in FP64 (after an FP64 polish if the double-float r itself
+    // is uncertain).
+    auto rbin_u = [&](int ps, int T, float* err) -> float {
+      const float rlh = (float)sh.rlo[T];
+      const float rll = (float)(sh.rlo[T] - (double)rlh);
+      const float ihr = (float)(1.0 / sh.hr[T]);
+      float dr = (r32[ps] - rlh) + (rl32[ps] - rll);
+      float u = dr * ihr;
+      *err = 4.0f * EPS32 * fabsf(u) + e32[ps] * ihr + 1e-6f;
+      return u;
+    };
     for (int ps = tid; ps < NP; ps += NT) {
       if (!(meta[ps] & M_VALID) || (meta[ps] & M_EXACT)) continue;
       int T = sh.runT[tb[ps]];
       double hr = sh.hr[T];
-      if (!(hr > 0.0) || hr * BR < (double)tiny) continue;
-      float u = (float)((double)r32[ps] - sh.rlo[T]) / (float)hr;
+      if (!(hr > 0.0) || hr * BR < (double)tiny || e32[ps] <= 1e-11f) continue;
+      float eu;
+      float u = rbin_u(ps, T, &eu);
       float fr = u - floorf(u);
-      float d = fminf(fr, 1.0f - fr);
-      float er = (e32[ps] + 8.0f * EPS32 * r32[ps]) / (float)hr + 1e-5f;
-      if (d <= er && u > 0.5f && u < (float)BR - 0.5f) q_push(sh, queue, ps);
+      if (fminf(fr, 1.0f - fr) <= eu && u > 0.5f && u < (float)BR - 0.5f) q_push(sh, queue, ps);
     }
     run_polish();
     for (int ps = tid; ps < NP; ps += NT) {
@@ -749,8 +777,13 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       double hr = sh.hr[T];
       int b;
       if (!(hr > 0.0)) b = 0;
-      else if (meta[ps] & M_EXACT) b = (int)floor((pr[pidx[ps]] - sh.rlo[T]) / hr);
-      else b = (int)floorf((float)((double)r32[ps] - sh.rlo[T]) / (float)hr);
+      else {
+        float eu;
+        float u = rbin_u(ps, T, &eu);
+        float fr = u - floorf(u);
+        if (fminf(fr, 1.0f - fr) > eu) b = (int)floorf(u);
+        else b = (int)floor((rv(ps) - sh.rlo[T]) / hr);
+      }
       b = min(max(b, 0), BR - 1);
       rb[ps] = (uint8_t)b;
       atomicOr(&sh.rocc[T], 1u << b);
@@ -759,6 +792,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     __syncthreads();
 
     if (diag_cnt && tid == 0) { long long c_ = clock64(); sh.cnt[8] = (int)min(c_ - sh.clk0, 2000000000LL); sh.clk0 = c_; }
+    if (diag_cnt && tid == 0) sh.cnt[15] = sh.cnt[0];
     // ------------------------------------------------ 6. gap probes, r runs, origin
     // One warp: for every theta run, every empty gap with points of a shared
     // theta bin on both sides is probed at its middle radius (FP32 with a
@@ -874,12 +908,16 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       bool ex = meta[ps] & M_EXACT;
       float er = ex ? 4.0f * EPS32 * r : e32[ps] + 4.0f * EPS32 * r;
       float et = ex ? 16.0f * EPS32 : e32[ps] / fmaxf(r, 1e-30f) + 16.0f * EPS32;
-      bool cand = fkey(r - er) <= sh.c_u[c][0] || fkey(r + er) >= sh.c_u[c][1] ||
-                  fkey(th - et) <= sh.c_u[c][2] || fkey(th + et) >= sh.c_u[c][3];
+      bool cand_r = fkey(r - er) <= sh.c_u[c][0] || fkey(r + er) >= sh.c_u[c][1];
+      bool cand_t = fkey(th - et) <= sh.c_u[c][2] || fkey(th + et) >= sh.c_u[c][3];
+      bool cand = cand_r || cand_t;
       float ext_r = fkey_inv(sh.c_u[c][1]) - fkey_inv(sh.c_u[c][0]);
       float ext_t = (fkey_inv(sh.c_u[c][3]) - fkey_inv(sh.c_u[c][2])) * r;
       bool is_tiny = ext_r < tiny && ext_t < tiny;
-      if (cand) { meta[ps] |= M_CAND; if (!ex && !is_tiny) q_push(sh, queue, ps); }
+      // theta extremes need an FP64 angle; r extremes only if the
+      // double-float r is uncertain
+      bool need = (cand_t && !sh.full) || !(e32[ps] <= 1e-11f);
+      if (cand) { meta[ps] |= M_CAND; if (!ex && !is_tiny && need) q_push(sh, queue, ps); }
     }
     run_polish();
     for (int ps = tid; ps < NP; ps += NT) {
@@ -1005,6 +1043,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       }
       __syncthreads();
       const int gth = sh.gth, gr = sh.gr, mth = sh.mth;
+      const float igth = 1.0f / (float)gth;
       // anchors (FP64, one per thread)
       for (int an = tid; an < sh.nanch; an += NT) {
         int gi = an / mth, mi = an % mth;
@@ -1050,68 +1089,84 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         for (int s0 = 0; s0 < NTH; s0 += seg) {
           const int s1 = min(s0 + seg, NTH);
           const int lo = s0 - 2, cnt = (s1 + 2) - lo;
-          // distances of the segment's rays and a 2-ray halo
-          for (int mi = lane; mi < cnt; mi += 32) {
-            int l = lo + mi;
-            float v;
-            if (!B.periodic && (l < 0 || l >= NTH)) {
-              v = __int_as_float(0x7f800000);  // beyond the grid edge
+          // signed squared distances of the segment's rays and a 2-ray halo
+          // (negative: inside the source; +inf: beyond a non-periodic grid
+          // edge); two independent rays per lane and iteration
+          auto ray_d2 = [&](int lw, float* d2o) -> bool {
+            int mgrp = __float2int_rz((float)lw * igth);
+            if (mgrp * gth > lw) --mgrp;
+            else if ((mgrp + 1) * gth <= lw) ++mgrp;
+            int o = lw - mgrp * gth;
+            const Anchor& an_ = anch[gi * mth + mgrp];
+            cf t = tab[o];
+            cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
+            cf U;
+            if constexpr (NL == 2) {
+              cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz;
+              float n0 = abs2(Q0), n1 = abs2(Q1);
+              float ip = __frcp_rn(n0 * n1);
+              cf t0 = an_.K[0] * cj(Q0), t1 = an_.K[1] * cj(Q1);
+              U = scl(scl(t0, n1) + scl(t1, n0), ip);
             } else {
-              int lw = l;
-              if (lw < 0) lw += NTH;
-              if (lw >= NTH) lw -= NTH;
-              int mgrp = lw / gth;
-              int o = lw - mgrp * gth;
-              const Anchor& an_ = anch[gi * mth + mgrp];
-              cf t = tab[o];
-              cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
-              cf U = mk(0.f, 0.f);
-              if constexpr (NL == 2) {
-                cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz;
-                float n0 = abs2(Q0), n1 = abs2(Q1);
-                float ip = 1.0f / (n0 * n1);
-                cf t0 = an_.K[0] * cj(Q0), t1 = an_.K[1] * cj(Q1);
-                U = scl(scl(t0, n1) + scl(t1, n0), ip);
-              } else {
-                cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz, Q2 = an_.A[2] + dz;
-                float n0 = abs2(Q0), n1 = abs2(Q1), n2 = abs2(Q2);
-                float n01 = n0 * n1;
-                float ip = 1.0f / (n01 * n2);
-                cf t0 = an_.K[0] * cj(Q0), t1 = an_.K[1] * cj(Q1), t2 = an_.K[2] * cj(Q2);
-                U = scl(scl(t0, n1 * n2) + scl(t1, n0 * n2) + scl(t2, n01), ip);
-              }
-              cf pz = dz * U;
-              cf dw = mk(an_.ws.x + dz.x + pz.x, an_.ws.y + dz.y - pz.y);
-              float d2 = abs2(dw);
-              float eb = fmaf(an_.e1, fabsf(U.x) + fabsf(U.y), an_.e0);
-              float gap = d2 - rho32 * rho32;
-              float d = sqrtf(d2);
-              bool in;
-              if (fabsf(gap) <= 2.0f * rho32 * eb + eb * eb) {
-                double d64 = ray_distance64<NL>(sh, B, i, lw);
-                if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
-                in = d64 < sh.rho;
-                d = (float)d64;
-              } else {
-                in = gap < 0.f;
-              }
-              v = in ? -d : d;
-              if (in && d == 0.f) v = -0.0f;
+              cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz, Q2 = an_.A[2] + dz;
+              float n0 = abs2(Q0), n1 = abs2(Q1), n2 = abs2(Q2);
+              float n01 = n0 * n1;
+              float ip = __frcp_rn(n01 * n2);
+              cf t0 = an_.K[0] * cj(Q0), t1 = an_.K[1] * cj(Q1), t2 = an_.K[2] * cj(Q2);
+              U = scl(scl(t0, n1 * n2) + scl(t1, n0 * n2) + scl(t2, n01), ip);
             }
-            buf[mi] = v;
+            cf pz = dz * U;
+            cf dw = mk(an_.ws.x + dz.x + pz.x, an_.ws.y + dz.y - pz.y);
+            float d2 = abs2(dw);
+            float eb = fmaf(an_.e1, fabsf(U.x) + fabsf(U.y), an_.e0);
+            *d2o = d2;
+            return fabsf(d2 - rho32 * rho32) <= 2.0f * rho32 * eb + eb * eb;  // FP32 cannot decide
+          };
+          auto wrapl = [&](int l) -> int { return l < 0 ? l + NTH : (l >= NTH ? l - NTH : l); };
+          for (int m0 = lane; m0 < cnt; m0 += 64) {
+            const int m1 = m0 + 32;
+            const int l0 = lo + m0, l1 = lo + m1;
+            const bool x0 = !B.periodic && (l0 < 0 || l0 >= NTH);
+            const bool x1 = m1 >= cnt || (!B.periodic && (l1 < 0 || l1 >= NTH));
+            const int lw0 = x0 ? 0 : wrapl(l0), lw1 = x1 ? 0 : wrapl(l1);
+            float a0, a1;
+            bool u0 = ray_d2(lw0, &a0);
+            bool u1 = ray_d2(lw1, &a1);
+            float v0 = a0 < rho32 * rho32 ? -a0 : a0;
+            float v1 = a1 < rho32 * rho32 ? -a1 : a1;
+            if (!x0 && u0) {
+              double d64 = ray_distance64<NL>(sh, B, i, lw0);
+              if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
+              float q = (float)(d64 * d64);
+              v0 = d64 < sh.rho ? -q : q;
+            }
+            if (!x1 && u1) {
+              double d64 = ray_distance64<NL>(sh, B, i, lw1);
+              if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
+              float q = (float)(d64 * d64);
+              v1 = d64 < sh.rho ? -q : q;
+            }
+            if (v0 == 0.f && a0 < rho32 * rho32) v0 = -0.0f;
+            if (v1 == 0.f && a1 < rho32 * rho32) v1 = -0.0f;
+            buf[m0] = x0 ? __int_as_float(0x7f800000) : v0;
+            if (m1 < cnt) buf[m1] = x1 ? __int_as_float(0x7f800000) : v1;
           }
           __syncwarp();
-          // per-point weights (Appendix A)
-          for (int mi = 2 + lane; mi < cnt - 2; mi += 32) {
-            float v = buf[mi];
-            if (!signbit(v)) continue;
-            float d = -v;
+          // per-point weights (Appendix A).  Points with both neighbours
+          // inside (W = 1) are summed directly; points next to the image
+          // boundary are queued per warp and their crossings solved with one
+          // point per lane.
+          auto brightness = [&](float d2) -> float {
+            if (g.uniform) return I0;
+            float x = fmaxf(0.f, 1.0f - d2 * irho2);
+            float sx = x > 0.f ? x * rsqrtf(x) : 0.f;
+            return I0 * (1.0f - u1f * (1.0f - sx));
+          };
+          auto boundary_weight = [&](int mi) -> float {
+            float d2 = -buf[mi];
             float vl = buf[mi - 1], vr = buf[mi + 1];
             bool Lin = signbit(vl), Rin = signbit(vr);
             float W;
-            if (Lin && Rin) {
-              W = 1.0f;
-            } else {
               float fL = 0.f, fR = 0.f;
               for (int side = 0; side < 2; ++side) {
                 bool isL = side == 0;
@@ -1130,11 +1185,11 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                     float vv = buf[mi + c0 + c];
                     if (isinf(vv)) { st_local |= ICRS_ST_EDGE; continue; }
                     xs[np_] = (float)(c0 + c);
-                    ys[np_] = fabsf(vv);
+                    ys[np_] = sqrtf(fabsf(vv));
                     ++np_;
                   }
                   float xo = isL ? -1.0f : 1.0f;
-                  float x = crossing_solve<float>(ys, xs[0], np_, d, fabsf(vo), xo, rho32, 1e-7f, 16);
+                  float x = crossing_solve<float>(ys, xs[0], np_, sqrtf(d2), sqrtf(fabsf(vo)), xo, rho32, 1e-5f, 12);
                   delta = isL ? -x : x;
                   if (!g.uniform && fabsf(delta - dcf) < 2e-3f) {
                     // branch of f(delta) too close to call in FP32: redo the
@@ -1168,14 +1223,36 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               if (Lin) W = fR;
               else if (Rin) W = fL;
               else W = fmaxf(0.f, fL + fR - 1.0f);
+            return W;
+          };
+          int* wq = wqueue + warp * 64;
+          int nq = 0;
+          for (int base = 2; base < cnt - 2; base += 32) {
+            const int mi = base + lane;
+            bool inside = false, edge = false;
+            if (mi < cnt - 2) {
+              float v = buf[mi];
+              inside = signbit(v);
+              if (inside) {
+                bool Lin = signbit(buf[mi - 1]), Rin = signbit(buf[mi + 1]);
+                if (Lin && Rin) rowacc += brightness(-v);
+                else edge = true;
+              }
             }
-            float I;
-            if (g.uniform) I = I0;
-            else {
-              float x = fmaxf(0.f, 1.0f - d * d * irho2);
-              I = I0 * (1.0f - u1f * (1.0f - sqrtf(x)));
+            unsigned msk = __ballot_sync(0xffffffffu, edge);
+            if (msk) {
+              int pos = nq + __popc(msk & ((1u << lane) - 1u));
+              if (edge) {
+                if (pos < 64) wq[pos] = mi;
+                else rowacc = fmaf(brightness(-buf[mi]), boundary_weight(mi), rowacc);
+              }
+              nq += __popc(msk);
             }
-            rowacc = fmaf(I, W, rowacc);
+          }
+          __syncwarp();
+          for (int q = lane; q < min(nq, 64); q += 32) {
+            int mi = wq[q];
+            rowacc = fmaf(brightness(-buf[mi]), boundary_weight(mi), rowacc);
           }
           __syncwarp();
         }
@@ -1324,14 +1401,15 @@ __global__ void point_source_kernel(const icrs_params* __restrict__ P, int S, co
 }
 
 // ---------------------------------------------------------------- host side
-static size_t mag_smem_bytes(int NL, const icrs_grid& g) {
+static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax) {
   const int N = NL * NL + 1;
   const size_t NP = (size_t)g.n_limb * N;
   size_t b = 0;
-  b += sizeof(cf) * NP + 3 * sizeof(float) * NP;
+  b += sizeof(cf) * NP + 4 * sizeof(float) * NP;
   b += sizeof(short) * ((NP + 7) & ~(size_t)7);
   b += 3 * ((NP + 15) & ~(size_t)15);
-  b += 2 * sizeof(double) * PMAX + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
+  b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
+  b += sizeof(int) * NW * 64;  // per-warp boundary queues
   b += sizeof(cf) * g.n_theta;
   const int seg = g.n_theta < 1024 ? g.n_theta : 1024;
   b += sizeof(float) * NW * (seg + 4);
@@ -1424,13 +1502,17 @@ static int launch_mag(const icrs_params* p, int S, const double* t, int E, const
   int nl = g->n_lens;
   if (nl == 0) { rc = first_n_lens(p, st, &nl); if (rc) return rc; }
   if (nl != 2 && nl != 3) return ICRS_EINVAL;
-  size_t smem = mag_smem_bytes(nl, *g);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return ICRS_ECUDA;
   int optin = 0, nsm = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  // the FP64 table takes whatever shared memory is left (up to 4096 entries)
+  int pmax = PMAX_MIN;
+  size_t smem = mag_smem_bytes(nl, *g, pmax);
   if (smem + sizeof(Shared) > (size_t)optin) return ICRS_EUNSUPPORTED;
+  while (pmax < 4096 && mag_smem_bytes(nl, *g, pmax * 2) + sizeof(Shared) <= (size_t)optin) pmax *= 2;
+  smem = mag_smem_bytes(nl, *g, pmax);
   cudaError_t ce;
   if (nl == 2) ce = cudaFuncSetAttribute(mag_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   else ce = cudaFuncSetAttribute(mag_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1446,9 +1528,9 @@ static int launch_mag(const icrs_params* p, int S, const double* t, int E, const
   if (per_block < 1) per_block = 1;
   long long blocks = (tiles + per_block - 1) / per_block;
   if (nl == 2)
-    mag_kernel<2><<<(unsigned)blocks, NT, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect, dcnt, dpts);
+    mag_kernel<2><<<(unsigned)blocks, NT, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect, dcnt, dpts, pmax);
   else
-    mag_kernel<3><<<(unsigned)blocks, NT, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect, dcnt, dpts);
+    mag_kernel<3><<<(unsigned)blocks, NT, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect, dcnt, dpts, pmax);
   return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
 }
 
