@@ -155,6 +155,50 @@ int icrs_magnification_diag(const icrs_params* p, int S, const double* t, int E,
                             double* sectors, int32_t* counters, float* points,
                             void* stream);
 
+/*
+ * Vector-Jacobian product of the finite-source magnification (binary lens)
+ * with respect to the 8 parameters, in this order:
+ *     (t0, tE, u0, alpha, s, q, rho, u1).
+ * The derivative is the exact derivative, almost everywhere, of the discrete
+ * method that icrs_magnification computes.  It runs through:
+ *   - the rays: the lens map, the brightness, the cubic boundary crossings and
+ *     f(delta) of Appendix A;
+ *   - the sector bounds: these move with their extremal image-limb points,
+ *     whose derivative is the implicit root derivative of Sec. 3.5, written
+ *     for the lens equation.
+ * The inclusion indicators and the binning decisions are piecewise constant,
+ * so they contribute nothing.  The kernel recomputes every ray instead of
+ * storing it: one fused forward and reverse pass per epoch.
+ *   p, S, t, E, g  as icrs_magnification (g->n_lens 2 or 0; triple lenses
+ *                  give ICRS_EUNSUPPORTED)
+ *   gA      [S][E] device double: upstream dL/dA (required when grad != NULL)
+ *   grad    [S][8] device double or NULL (out): sum_e gA[s][e] dA[s][e]/dp.
+ *           It is zeroed on `stream`, then accumulated with atomics, so the
+ *           order of the floating-point sums is not fixed.
+ *   dA      [S][E][8] device double or NULL (out): per-epoch dA/dp
+ *   A       [S][E] device double or NULL (out): the magnification
+ *   status  [S][E] device uint32 or NULL (out), as icrs_magnification
+ * At least one of grad and dA must be non-NULL.
+ */
+int icrs_magnification_vjp(const icrs_params* p, int S, const double* t, int E,
+                           const icrs_grid* g, const double* gA, double* grad,
+                           double* dA, double* A, uint32_t* status, void* stream);
+
+/*
+ * chi^2 of S light curves and its gradient with respect to the 8 parameters
+ * of icrs_magnification_vjp.  The flux model is F = (A - 1) F_S + F_base with
+ * F_S = F_base = 1, so F = A:
+ *     chi2[s] = sum_e ((y[s][e] - A[s][e]) / sigma[s][e])^2.
+ *   y, sigma  [S][E] device double: observed flux and its error (sigma > 0)
+ *   chi2      [S] device double (out; zeroed on `stream`, then accumulated)
+ *   grad      [S][8] device double (out; zeroed, then accumulated)
+ *   A, status optional outputs, as in icrs_magnification_vjp
+ */
+int icrs_chi2_grad(const icrs_params* p, int S, const double* t, int E,
+                   const icrs_grid* g, const double* y, const double* sigma,
+                   double* chi2, double* grad, double* A, uint32_t* status,
+                   void* stream);
+
 /* Message for a return code (static string). */
 const char* icrs_strerror(int code);
 

@@ -31,6 +31,7 @@
 #include "icrs.h"
 #include "icrs_common.cuh"
 #include "icrs_df64.cuh"
+#include "icrs_sectors.cuh"
 
 namespace icrs {
 
@@ -43,6 +44,8 @@ constexpr int MAXRB = 32;        // r bins per theta run
 constexpr int MAXCELL = 96;      // (theta run, r run) cells
 constexpr int MAXBOX = 96;       // candidate sectors before merging
 constexpr int MAXANCH = 128;     // FP64 anchors per sector
+constexpr int MAXCELL_D = 40;    // cells with tracked derivatives
+constexpr int MAXBOX_D = 40;     // candidate sectors with tracked derivatives
 constexpr float TINY_EXTENT = 3e-4f;  // images smaller than this x rho skip FP64 decisions
 constexpr float EPS32 = 5.9604645e-8f;  // 2^-24
 
@@ -57,10 +60,7 @@ struct Anchor {
   float e1;     // error bound factor of |U|_1
 };
 
-struct Box {
-  double r_lo, r_hi, th_lo, width;
-  int periodic;
-};
+using Box = BoxT<double>;
 
 struct Shared {
   // ---- per parameter set
@@ -112,6 +112,21 @@ struct Shared {
   double red[NW];
 };
 
+// Derivative-mode state (binary lens), in the dynamic shared memory of that
+// instantiation only.
+struct DerShared {
+  int cell_arg[MAXCELL_D][4];  // slot of the point that sets each cell extreme
+  double Gb[MAXBOX_D][4];   // dS / d(r_lo, r_hi, th_lo, width) of each sector
+  double H[8];              // dS / d(w_c.x, w_c.y, rho, u1, a1.x, a2.x, eps1, eps2)
+  cd dwc[4];                // d w_c / d(t0, tE, u0, alpha)
+  double dadp[2][2];        // d a_j.x / d(s, q)
+  double depsq[2];          // d eps_j / d q
+  DualD cx[MAXCELL_D * 4];  // cell extremes with tangents
+  BoxT<DualD> box[MAXBOX_D];  // sectors with tangents
+  double wder[NW][12];      // per-warp sums of the row derivatives
+  float2 acs[MAXANCH];      // cos, sin of each anchor angle
+};
+
 // Order-preserving integer keys for signed FP32 / FP64 values.
 __device__ __forceinline__ unsigned int fkey(float v) {
   unsigned int u = __float_as_uint(v);
@@ -130,11 +145,6 @@ __device__ __forceinline__ double dkey_inv(unsigned long long k) {
   return __longlong_as_double((long long)u);
 }
 
-__device__ __forceinline__ double wrap_pi(double a) {
-  double x = fmod(a + kPi, 2.0 * kPi);
-  if (x < 0) x += 2.0 * kPi;
-  return x - kPi;
-}
 
 // ---------------------------------------------------------------- FP64 paths
 // Limb point k in FP64 (Sec. 3.2).
@@ -221,6 +231,65 @@ __device__ inline double ray_distance64(const Shared& sh, const Box& B, int i, i
   return sqrt(abs2(w - sh.wc));
 }
 
+// Tangents of an image-limb point z = r e^{i th} (the image of the source-limb
+// point w_c + rho u) with respect to (t0, tE, u0, alpha, s, q, rho, u1), binary
+// lens: the implicit derivative of the lens equation F(z; p) = f(z; p) - w(p)
+// = 0, dz = -J^{-1} dF/dp at fixed z, J the real 2x2 Jacobian of f (the root
+// derivative of Sec. 3.5, written for the lens equation rather than the
+// polynomial so that it holds in any frame).  Returns d r / dp and d th / dp.
+__device__ inline void point_tangents(const Shared& sh, const DerShared& ds, double r, double th, cd u, double* dr,
+                                      double* dth) {
+  double sn, cs;
+  sincos(th, &sn, &cs);
+  const cd z = mk(r * cs, r * sn);
+  cd gm = mk(0.0, 0.0), cA[2], cE[2];
+  for (int j = 0; j < 2; ++j) {
+    cd iv = inv(z - sh.L.a[j]);
+    cd iv2 = iv * iv;
+    gm = gm + scl(iv2, sh.L.eps[j]);
+    cA[j] = scl(cj(iv2), -sh.L.eps[j]);  // df/da_j.x = -eps_j / conj(z - a_j)^2
+    cE[j] = scl(cj(iv), -1.0);           // df/deps_j = -1 / conj(z - a_j)
+  }
+  // df = dz + conj(gamma) conj(dz):  J = [[1 + g.x, -g.y], [-g.y, 1 - g.x]]
+  const double j11 = 1.0 + gm.x, j12 = -gm.y, j22 = 1.0 - gm.x;
+  const double det = j11 * j22 - j12 * j12;
+  for (int q = 0; q < NPAR; ++q) {
+    cd dF = mk(0.0, 0.0);
+    if (q < 4) dF = scl(ds.dwc[q], -1.0);
+    else if (q == 4) dF = scl(cA[0], ds.dadp[0][0]) + scl(cA[1], ds.dadp[1][0]);
+    else if (q == 5) dF = scl(cA[0], ds.dadp[0][1]) + scl(cA[1], ds.dadp[1][1]) + scl(cE[0], ds.depsq[0]) + scl(cE[1], ds.depsq[1]);
+    else if (q == 6) dF = scl(u, -1.0);
+    double dx = -(j22 * dF.x - j12 * dF.y) / det;
+    double dy = -(-j12 * dF.x + j11 * dF.y) / det;
+    dr[q] = (z.x * dx + z.y * dy) / r;
+    dth[q] = (z.x * dy - z.y * dx) / (r * r);
+  }
+}
+
+// Lagrange basis of the nodes 0 .. npt-1 (npt = 2..4) at t, and the slope
+// of the interpolant through y there.
+template <class T>
+__device__ inline T lagrange_basis(const T* y, int npt, T t, T* l) {
+  const T d1 = y[1] - y[0];
+  const T d2 = npt > 2 ? T(0.5) * (y[2] - T(2) * y[1] + y[0]) : T(0);
+  const T d3 = npt > 3 ? (y[3] - T(3) * y[2] + T(3) * y[1] - y[0]) * T(1.0 / 6.0) : T(0);
+  const T t1 = t - T(1), t2 = t - T(2), t3 = t - T(3);
+  if (npt == 4) {
+    l[0] = -t1 * t2 * t3 * T(1.0 / 6.0);
+    l[1] = T(0.5) * t * t2 * t3;
+    l[2] = T(-0.5) * t * t1 * t3;
+    l[3] = t * t1 * t2 * T(1.0 / 6.0);
+  } else if (npt == 3) {
+    l[0] = T(0.5) * t1 * t2;
+    l[1] = -t * t2;
+    l[2] = T(0.5) * t * t1;
+  } else {
+    l[0] = -t1;
+    l[1] = t;
+  }
+  return d1 + (T(2) * t - T(1)) * d2 + ((T(3) * t - T(6)) * t + T(2)) * d3;
+}
+
 // ---------------------------------------------------------------- queue
 __device__ __forceinline__ void q_push(Shared& sh, int* queue, int v) {
   int i = atomicAdd(&sh.qn, 1);
@@ -272,12 +341,38 @@ __device__ __forceinline__ T fdelta(T d, T delta_c, int uniform) {
   return T(2.0 / 3.0) * d + T(0.5);
 }
 
+// f'(delta) of the rule above.
+template <class T>
+__device__ __forceinline__ T fdelta_prime(T d, T delta_c, int uniform) {
+  if (uniform) return T(1);
+  if (d >= delta_c) {
+    T h = T(1) + T(1) / (T(2) * d);
+    T sq = sqrt(h);
+    return T(2.0 / 3.0) * sq - (T(0.5) + d) / (T(6) * d * d * sq);
+  }
+  return T(2.0 / 3.0);
+}
+
 // ---------------------------------------------------------------- kernel
-template <int NL>
+// DER = true: also the derivative of A with respect to (t0, tE, u0, alpha, s,
+// q, rho, u1) (binary lens): reverse mode over the rays (adjoint seeds per
+// ray, then each seeded ray's gradient), forward mode (8 tangents) over the
+// sector bounds via the implicit derivative of the extremal image points.
+struct DerOut {
+  const double* gA;    // [S][E] upstream dL/dA, or NULL
+  const double* yobs;  // [S][E] data for chi^2 (with sig), or NULL
+  const double* sig;   // [S][E]
+  double* dA;          // [S][E][8] or NULL
+  double* grad;        // [S][8] accumulated, or NULL
+  double* chi2;        // [S] accumulated, or NULL
+};
+
+template <int NL, bool DER>
 __global__ void __launch_bounds__(NT, 1)
 mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ T_, int E,
            icrs_grid g, int tiles_per_block, double* __restrict__ A_out, uint32_t* __restrict__ st_out,
-           double* __restrict__ diag_sect, int32_t* __restrict__ diag_cnt, float* __restrict__ diag_pts, int PMAX) {
+           double* __restrict__ diag_sect, int32_t* __restrict__ diag_cnt, float* __restrict__ diag_pts, int PMAX,
+           int has_plo, DerOut dout) {
   constexpr int N = NL * NL + 1;
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Shared sh;
@@ -292,6 +387,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   // lens's frame (also the next epoch's warm start), FP32 (r, theta), FP32
   // error bound, flags, bins, index into the FP64 table
   cf* phi = (cf*)p;              p += sizeof(cf) * NP;
+  cf* plo = (cf*)p;              p += has_plo ? sizeof(cf) * NP : 0;   // lo part of refined positions
   float* r32 = (float*)p;        p += sizeof(float) * NP;
   float* rl32 = (float*)p;       p += sizeof(float) * NP;   // r = r32 + rl32 (double-float)
   float* t32 = (float*)p;        p += sizeof(float) * NP;
@@ -308,7 +404,13 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   const int seg = g.n_theta < 1024 ? g.n_theta : 1024;
   float* rowbuf = (float*)p;     p += sizeof(float) * NW * (seg + 4);
   cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
-  int* wqueue = (int*)p;         // NW x 64 boundary points of the current row
+  int* wqueue = (int*)p;         p += sizeof(int) * NW * 64;  // boundary points of the current row
+  // derivative mode: its state and the per-warp ray seeds
+  DerShared& ds = *(DerShared*)p;  p += DER ? sizeof(DerShared) : 0;
+  DualD* cdual = ds.cx;
+  BoxT<DualD>* bdual = ds.box;
+  double* wder = &ds.wder[0][0];
+  float* abuf = (float*)p;       // NW x (seg + 4) adjoint seeds
 
   if (tid == 0) { sh.cur_set = -1; sh.warm = 0; }
   for (int k = tid; k < K; k += NT) {
@@ -359,6 +461,27 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         sh.warm = 1;  // previous tile of this block was the previous epoch of this set
       }
       sh.wc = source_centre(P[s], T_[(size_t)s * E + e]);
+      if (DER) {
+        // d w_c / d(t0, tE, u0, alpha) and d(a_j, eps_j) / d(s, q) (binary):
+        // w_c = tau (cos a, sin a) + u0 (-sin a, cos a), tau = (t - t0) / tE;
+        // a_1 = -q s / (1 + q), a_2 = s / (1 + q), eps_1 = 1 / (1 + q),
+        // eps_2 = q / (1 + q)
+        const icrs_params& pp = P[s];
+        double tau = (T_[(size_t)s * E + e] - pp.t0) / pp.tE;
+        double sa, ca;
+        sincos(pp.alpha, &sa, &ca);
+        ds.dwc[0] = mk(-ca / pp.tE, -sa / pp.tE);
+        ds.dwc[1] = mk(-tau * ca / pp.tE, -tau * sa / pp.tE);
+        ds.dwc[2] = mk(-sa, ca);
+        ds.dwc[3] = mk(-tau * sa - pp.u0 * ca, tau * ca - pp.u0 * sa);
+        double oq = 1.0 + pp.q;
+        ds.dadp[0][0] = -pp.q / oq;  ds.dadp[0][1] = -pp.s / (oq * oq);
+        ds.dadp[1][0] = 1.0 / oq;    ds.dadp[1][1] = -pp.s / (oq * oq);
+        ds.depsq[0] = -1.0 / (oq * oq);
+        ds.depsq[1] = 1.0 / (oq * oq);
+        for (int b = 0; b < MAXBOX_D; ++b) for (int k = 0; k < 4; ++k) ds.Gb[b][k] = 0.0;
+        for (int k = 0; k < 8; ++k) ds.H[k] = 0.0;
+      }
       for (int j = 0; j < NL; ++j) {
         cd d = sh.wc - sh.L.a[j];
         sh.wcj32[j] = tof(d);
@@ -517,8 +640,10 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         cf F = mk(Fx.hi + Fx.lo, Fy.hi + Fy.lo);
         float res = sqrtf(abs2(F));
         // position kept for an FP64 decision if needed
-        df px = two_sum(x.x, sh.aj32[ll][nj].x);
-        df py = two_sum(x.y, sh.aj32[ll][nj].y);
+        // position of this root in the lightest lens's frame, double-float:
+        // x (exact float) + (a_nj - a_ll) (double-float)
+        df px = df_add(df_make(x.x, 0.f), sh.adf[ll][nj][0]);
+        df py = df_add(df_make(x.y, 0.f), sh.adf[ll][nj][1]);
         if (!(res == res) || res > 0.25f * img_tol) {
           if (!(res >= 4.0f * img_tol)) {  // FP64 decides
             meta[pslot] = M_UNSURE;
@@ -559,6 +684,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         }
         meta[pslot] = M_VALID;
         phi[pslot] = mk(px.hi, py.hi);
+        if (has_plo) plo[pslot] = mk(px.lo, py.lo);
         r32[pslot] = rr;
         rl32[pslot] = rlo;
         t32[pslot] = th;
@@ -612,10 +738,17 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         if (meta[ps] & M_EXACT) continue;
         int k = ps / N;
         atomicAdd(&sh.cnt[0], 1);
-        cd w = limb_point64(sh, k, K);
-        cd z0 = tod(phi[ps]) + sh.L.a[ll];
         double r, th;
-        polish_image64<NL>(sh, z0, w, &r, &th);
+        if (has_plo && e32[ps] <= 1e-11f) {
+          // the double-float position is already accurate to ~1e-12
+          cd z0 = mk((double)phi[ps].x + (double)plo[ps].x, (double)phi[ps].y + (double)plo[ps].y) + sh.L.a[ll];
+          r = sqrt(z0.x * z0.x + z0.y * z0.y);
+          th = atan2(z0.y, z0.x);
+        } else {
+          cd w = limb_point64(sh, k, K);
+          cd z0 = tod(phi[ps]) + sh.L.a[ll];
+          polish_image64<NL>(sh, z0, w, &r, &th);
+        }
         int pi = atomicAdd(&sh.pn, 1);
         if (pi < PMAX) {
           pr[pi] = r; pt[pi] = th; pidx[ps] = (short)pi;
@@ -869,6 +1002,11 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           sh.c_u[c][0] = 0xffffffffu; sh.c_u[c][1] = 0u; sh.c_u[c][2] = 0xffffffffu; sh.c_u[c][3] = 0u;
           sh.c_x[c][0] = ~0ull; sh.c_x[c][1] = 0ull; sh.c_x[c][2] = ~0ull; sh.c_x[c][3] = 0ull;
         }
+        if (DER) {
+          for (int c = 0; c < MAXCELL_D; ++c)
+            for (int k = 0; k < 4; ++k) ds.cell_arg[c][k] = 0x7fffffff;
+          if (tot > MAXCELL_D) atomicOr(&sh.status, ICRS_ST_OVERFLOW);
+        }
       }
     }
     __syncthreads();
@@ -931,84 +1069,90 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       atomicMax(&sh.c_x[c][3], dkey(th));
     }
     __syncthreads();
+    if (DER) {
+      // the point that sets each cell extreme (lowest slot on ties), then
+      // the extremes as dual numbers carrying that point's tangents
+      for (int ps = tid; ps < NP; ps += NT) {
+        if (!(meta[ps] & M_VALID)) continue;
+        int c = cell_of(ps);
+        if (c >= MAXCELL_D) continue;
+        unsigned long long kr = dkey(rv(ps)), kt = dkey(unwrap_t(ps, tv(ps)));
+        if (kr == sh.c_x[c][0]) atomicMin(&ds.cell_arg[c][0], ps);
+        if (kr == sh.c_x[c][1]) atomicMin(&ds.cell_arg[c][1], ps);
+        if (kt == sh.c_x[c][2]) atomicMin(&ds.cell_arg[c][2], ps);
+        if (kt == sh.c_x[c][3]) atomicMin(&ds.cell_arg[c][3], ps);
+      }
+      __syncthreads();
+      const int nd = min(sh.ncell, MAXCELL_D) * 4;
+      for (int idx = tid; idx < nd; idx += NT) {
+        const int c = idx >> 2, k = idx & 3;
+        DualD v = dconst(dkey_inv(sh.c_x[c][k]));
+        const int ps = ds.cell_arg[c][k];
+        if (sh.c_cnt[c] && ps < NP) {
+          const int kl = ps / N;
+          cd u = mk((double)ulimb[kl].x.hi + (double)ulimb[kl].x.lo, (double)ulimb[kl].y.hi + (double)ulimb[kl].y.lo);
+          // tangents at the FP64 position (the value stays the extreme the
+          // sectors were built from)
+          double r_ = rv(ps), t_ = tv(ps);
+          if (!(meta[ps] & M_EXACT)) {
+            cd z0 = tod(phi[ps]);
+            if (has_plo) z0 = z0 + tod(plo[ps]);
+            polish_image64<NL>(sh, z0 + sh.L.a[ll], limb_point64(sh, kl, K), &r_, &t_);
+          }
+          double dr_[NPAR], dt_[NPAR];
+          point_tangents(sh, ds, r_, t_, u, dr_, dt_);
+          for (int q = 0; q < NPAR; ++q) v.d[q] = k < 2 ? dr_[q] : dt_[q];
+        }
+        cdual[idx] = v;
+      }
+      __syncthreads();
+    }
 
     if (diag_cnt && tid == 0) { long long c_ = clock64(); sh.cnt[10] = (int)min(c_ - sh.clk0, 2000000000LL); sh.clk0 = c_; }
     // ------------------------------------------------ 8. sectors (FP64, one thread)
-    if (tid == 0) {
+    if (tid == 0 && !DER) {
       int nb = 0;
-      const double m = g.margin;
       for (int T = 0; T < nT; ++T) {
         int c0 = sh.cellbase[T], c1 = sh.cellbase[T + 1];
         for (int c = c0; c < c1 && c < MAXCELL; ++c) {
           if (!sh.c_cnt[c]) continue;
-          double rmin = dkey_inv(sh.c_x[c][0]), rmax = dkey_inv(sh.c_x[c][1]);
-          double tmin = dkey_inv(sh.c_x[c][2]), tmax = dkey_inv(sh.c_x[c][3]);
-          Box B;
-          double er = rmax - rmin;
-          B.r_lo = rmin - m * er;
-          if (B.r_lo < 0.0) B.r_lo = 0.0;
-          B.r_hi = rmax + m * er;
-          if (sh.origin_in && c == c0) B.r_lo = 0.0;
-          double et = tmax - tmin;
-          double lo = tmin - m * et, wd = et + 2.0 * m * et;
-          if (sh.full || wd >= 2.0 * kPi) { B.periodic = 1; B.th_lo = -kPi; B.width = 2.0 * kPi; }
-          else { B.periodic = 0; B.th_lo = lo + (wrap_pi(lo) - lo); B.width = wd; }
+          Box B = cell_box<double>(dkey_inv(sh.c_x[c][0]), dkey_inv(sh.c_x[c][1]), dkey_inv(sh.c_x[c][2]),
+                                   dkey_inv(sh.c_x[c][3]), g.margin, sh.full != 0, sh.origin_in && c == c0);
           if (nb < MAXBOX) sh.box[nb++] = B;
           else sh.status |= ICRS_ST_OVERFLOW;
         }
       }
-      // merge overlapping sectors until none overlap; then cap at N_deg
-      auto overlap = [](const Box& a, const Box& b) -> bool {
-        if (!(a.r_lo < b.r_hi && b.r_lo < a.r_hi)) return false;
-        if (a.periodic || b.periodic) return true;
-        double d = fmod(b.th_lo - a.th_lo, 2.0 * kPi);
-        if (d < 0) d += 2.0 * kPi;
-        return d < a.width || d + b.width > 2.0 * kPi;
-      };
-      auto unite = [](const Box& a, const Box& b) -> Box {
-        Box u;
-        u.r_lo = fmin(a.r_lo, b.r_lo);
-        u.r_hi = fmax(a.r_hi, b.r_hi);
-        if (a.periodic || b.periodic) { u.periodic = 1; u.th_lo = -kPi; u.width = 2.0 * kPi; return u; }
-        double dv_ = fmod(b.th_lo - a.th_lo, 2.0 * kPi);
-        if (dv_ < 0) dv_ += 2.0 * kPi;
-        double d = b.th_lo - a.th_lo + (dv_ - (b.th_lo - a.th_lo));
-        double wdt, start;
-        if (dv_ < a.width) { start = a.th_lo; wdt = fmax(a.width, d + b.width); }
-        else { start = a.th_lo + d - 2.0 * kPi; wdt = fmax(a.width + 2.0 * kPi - d, b.width); }
-        if (wdt >= 2.0 * kPi) { u.periodic = 1; u.th_lo = -kPi; u.width = 2.0 * kPi; }
-        else { u.periodic = 0; u.th_lo = start + (wrap_pi(start) - start); u.width = wdt; }
-        return u;
-      };
-      auto area = [](const Box& b) -> double { return 0.5 * (b.r_hi * b.r_hi - b.r_lo * b.r_lo) * b.width; };
-      for (;;) {
-        bool merged = false;
-        for (int i = 0; i < nb && !merged; ++i)
-          for (int j = i + 1; j < nb && !merged; ++j)
-            if (overlap(sh.box[i], sh.box[j])) {
-              sh.box[i] = unite(sh.box[i], sh.box[j]);
-              for (int k = j; k < nb - 1; ++k) sh.box[k] = sh.box[k + 1];
-              --nb;
-              merged = true;
-            }
-        if (merged) continue;
-        if (nb <= N) break;
-        sh.status |= ICRS_ST_SECTCAP;
-        int bi = 0, bj = 1;
-        double best = 0.0;
-        bool have = false;
-        for (int i = 0; i < nb; ++i)
-          for (int j = i + 1; j < nb; ++j) {
-            Box u = unite(sh.box[i], sh.box[j]);
-            double cost = area(u) - area(sh.box[i]) - area(sh.box[j]);
-            if (!have || cost < best) { best = cost; bi = i; bj = j; have = true; }
-          }
-        sh.box[bi] = unite(sh.box[bi], sh.box[bj]);
-        for (int k = bj; k < nb - 1; ++k) sh.box[k] = sh.box[k + 1];
-        --nb;
+      bool capped = false;
+      nb = merge_boxes<double>(sh.box, nb, N, &capped);
+      if (capped) sh.status |= ICRS_ST_SECTCAP;
+      sh.nbox = nb;
+    }
+    if (tid == 0 && DER) {
+      // the same rules on dual numbers: the sector bounds and their tangents
+      int nb = 0;
+      for (int T = 0; T < nT; ++T) {
+        int c0 = sh.cellbase[T], c1 = sh.cellbase[T + 1];
+        for (int c = c0; c < c1 && c < MAXCELL; ++c) {
+          if (!sh.c_cnt[c]) continue;
+          if (c >= MAXCELL_D || nb >= MAXBOX_D) { sh.status |= ICRS_ST_OVERFLOW; continue; }
+          bdual[nb++] = cell_box<DualD>(cdual[c * 4 + 0], cdual[c * 4 + 1], cdual[c * 4 + 2], cdual[c * 4 + 3],
+                                        g.margin, sh.full != 0, sh.origin_in && c == c0);
+        }
+      }
+      bool capped = false;
+      nb = merge_boxes<DualD>(bdual, nb, N, &capped);
+      if (capped) sh.status |= ICRS_ST_SECTCAP;
+      for (int b = 0; b < nb; ++b) {
+        sh.box[b].r_lo = bdual[b].r_lo.v;
+        sh.box[b].r_hi = bdual[b].r_hi.v;
+        sh.box[b].th_lo = bdual[b].th_lo.v;
+        sh.box[b].width = bdual[b].width.v;
+        sh.box[b].periodic = bdual[b].periodic;
       }
       sh.nbox = nb;
     }
+    if (DER)
+      for (int k = tid; k < NW * 12; k += NT) wder[k] = 0.0;
     __syncthreads();
 
     if (diag_cnt && tid == 0) { long long c_ = clock64(); sh.cnt[11] = (int)min(c_ - sh.clk0, 2000000000LL); sh.clk0 = c_; }
@@ -1059,7 +1203,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         for (int j = 0; j < NL; ++j) {
           cd Aj = R * (zc - sh.L.a[j]);
           an_.A[j] = tof(Aj);
-          an_.K[j] = tof(scl(inv(Aj), sh.L.eps[j]));
+          an_.K[j] = scl(inv(an_.A[j]), sh.eps32[j]);  // FP32 suffices (relative error of the U term)
         }
         // error bound of |Delta w'|: anchor term plus rounding of the ray's
         // offset (at most the group half-diagonal) and of its image term
@@ -1067,6 +1211,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         an_.e0 = (float)(16.0 * EPS32 * (fabs(an_.ws.x) + fabs(an_.ws.y) + 2.0 * half));
         an_.e1 = (float)(16.0 * EPS32 * half);
         anch[an] = an_;
+        if (DER) ds.acs[an] = make_float2((float)cs, (float)sn);
       }
       // offsets within a theta group: (cos d - 1, sin d), d = (o + 1/2 - gth/2) dth
       for (int o = tid; o < gth; o += NT) {
@@ -1086,6 +1231,12 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         const double rc64 = B.r_lo + (gi * gr + 0.5 * gr) * sh.dr64;
         const float ri = (float)(rc64) + dri;
         float rowacc = 0.f;
+        // derivative mode, this lane's part of the row: sum a dd/dr_i, sum a
+        // dd/dth_l, sum a dd/dth_l (l + 1/2), then dRow/d(w_c.x, w_c.y, rho,
+        // u1, a1.x, a2.x, eps1, eps2); a = dRow/dd_l the seed of ray l
+        float pg[11];
+        if (DER)
+          for (int k = 0; k < 11; ++k) pg[k] = 0.f;
         for (int s0 = 0; s0 < NTH; s0 += seg) {
           const int s1 = min(s0 + seg, NTH);
           const int lo = s0 - 2, cnt = (s1 + 2) - lo;
@@ -1151,6 +1302,9 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             buf[m0] = x0 ? __int_as_float(0x7f800000) : v0;
             if (m1 < cnt) buf[m1] = x1 ? __int_as_float(0x7f800000) : v1;
           }
+          float* ab = abuf + warp * (seg + 4);
+          if (DER)
+            for (int m = lane; m < cnt; m += 32) ab[m] = 0.f;
           __syncwarp();
           // per-point weights (Appendix A).  Points with both neighbours
           // inside (W = 1) are summed directly; points next to the image
@@ -1162,12 +1316,34 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             float sx = x > 0.f ? x * rsqrtf(x) : 0.f;
             return I0 * (1.0f - u1f * (1.0f - sx));
           };
+          // I and dI/dd, dI/drho, dI/du1 at squared distance d2 (linear law:
+          // I = I0 (1 - u1 + u1 sqrt(1 - d^2/rho^2)), I0 = 3 / (pi (3 - u1)))
+          auto brightness_der = [&](float d2, float* Id, float* Ir, float* Iu) -> float {
+            if (g.uniform) { *Id = 0.f; *Ir = 0.f; *Iu = 0.f; return I0; }
+            float x = fmaxf(0.f, 1.0f - d2 * irho2);
+            float sx = x > 0.f ? x * rsqrtf(x) : 0.f;
+            float I = I0 * (1.0f - u1f * (1.0f - sx));
+            float d = sqrtf(d2);
+            float k = sx > 0.f ? I0 * u1f * irho2 / sx : 0.f;
+            *Id = -k * d;
+            *Ir = k * d2 / rho32;
+            *Iu = I / (3.0f - u1f) + I0 * (sx - 1.0f);
+            return I;
+          };
+          // derivative mode: per side, d delta / d(stencil distances) and
+          // d delta / d rho times f'(delta) (crossing p(x) = rho, dx = (drho -
+          // sum_m l_m(x) dy_m) / p'(x); delta = -x on the left, x on the right).
+          // p'(x) is a difference of nearly equal distances, so the stencil
+          // and the crossing are taken in FP64 in this mode.
+          float sd_c[2], sd_l[2][4];
+          int sd_b[2], sd_n[2];
           auto boundary_weight = [&](int mi) -> float {
             float d2 = -buf[mi];
             float vl = buf[mi - 1], vr = buf[mi + 1];
             bool Lin = signbit(vl), Rin = signbit(vr);
             float W;
               float fL = 0.f, fR = 0.f;
+              if (DER) { sd_n[0] = sd_n[1] = 0; sd_c[0] = sd_c[1] = 0.f; }
               for (int side = 0; side < 2; ++side) {
                 bool isL = side == 0;
                 if (isL ? Lin : Rin) continue;
@@ -1176,6 +1352,33 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                 if (isinf(vo)) {
                   delta = 0.5f;
                   st_local |= ICRS_ST_EDGE;
+                } else if (DER) {
+                  const int c0 = isL ? -2 : -1;
+                  const int l = lo + mi;
+                  double xsd[4], ysd[4], l64[4];
+                  int nd = 0;
+                  double yin = 0, yout = 0;
+                  for (int c = 0; c < 4; ++c) {
+                    int ll2 = l + c0 + c;
+                    if (!B.periodic && (ll2 < 0 || ll2 >= NTH)) { st_local |= ICRS_ST_EDGE; continue; }
+                    int lw2 = ((ll2 % NTH) + NTH) % NTH;
+                    xsd[nd] = (double)(c0 + c);
+                    ysd[nd] = ray_distance64<NL>(sh, B, i, lw2);
+                    if (c0 + c == 0) yin = ysd[nd];
+                    if (c0 + c == (isL ? -1 : 1)) yout = ysd[nd];
+                    ++nd;
+                  }
+                  double xd = crossing_solve<double>(ysd, xsd[0], nd, yin, yout, isL ? -1.0 : 1.0, sh.rho, 1e-14, 60);
+                  double dd = isL ? -xd : xd;
+                  float fv = (float)fdelta<double>(dd, g.delta_c, g.uniform);
+                  if (isL) fL = fv; else fR = fv;
+                  double slope = lagrange_basis<double>(ysd, nd, xd - xsd[0], l64);
+                  double fp = fdelta_prime<double>(dd, g.delta_c, g.uniform);
+                  sd_c[side] = (float)((isL ? -fp : fp) / slope);
+                  for (int m = 0; m < nd; ++m) sd_l[side][m] = (float)l64[m];
+                  sd_b[side] = mi + (int)xsd[0];
+                  sd_n[side] = nd;
+                  continue;
                 } else {
                   // stencil: entering (-2,-1,0,+1), exiting (-1,0,+1,+2)
                   float xs[4], ys[4];
@@ -1223,7 +1426,25 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               if (Lin) W = fR;
               else if (Rin) W = fL;
               else W = fmaxf(0.f, fL + fR - 1.0f);
+              if (DER && !(Lin || Rin) && !(fL + fR - 1.0f > 0.f)) sd_n[0] = sd_n[1] = 0, sd_c[0] = sd_c[1] = 0.f;
             return W;
+          };
+          // contribution I W of boundary point mi; derivative mode: its seeds
+          auto boundary_point = [&](int mi) -> float {
+            if (!DER) return brightness(-buf[mi]) * boundary_weight(mi);
+            float Id, Ir, Iu;
+            float I = brightness_der(-buf[mi], &Id, &Ir, &Iu);
+            float W = boundary_weight(mi);
+            atomicAdd(&ab[mi], W * Id);
+            pg[5] += W * Ir;
+            pg[6] += W * Iu;
+            for (int sd = 0; sd < 2; ++sd) {
+              if (!sd_n[sd]) continue;
+              const float c = I * sd_c[sd];
+              pg[5] += c;
+              for (int m = 0; m < sd_n[sd]; ++m) atomicAdd(&ab[sd_b[sd] + m], -c * sd_l[sd][m]);
+            }
+            return I * W;
           };
           int* wq = wqueue + warp * 64;
           int nq = 0;
@@ -1235,8 +1456,19 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               inside = signbit(v);
               if (inside) {
                 bool Lin = signbit(buf[mi - 1]), Rin = signbit(buf[mi + 1]);
-                if (Lin && Rin) rowacc += brightness(-v);
-                else edge = true;
+                if (Lin && Rin) {
+                  if (DER) {
+                    float Id, Ir, Iu;
+                    rowacc += brightness_der(-v, &Id, &Ir, &Iu);
+                    atomicAdd(&ab[mi], Id);
+                    pg[5] += Ir;
+                    pg[6] += Iu;
+                  } else {
+                    rowacc += brightness(-v);
+                  }
+                } else {
+                  edge = true;
+                }
               }
             }
             unsigned msk = __ballot_sync(0xffffffffu, edge);
@@ -1244,17 +1476,87 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               int pos = nq + __popc(msk & ((1u << lane) - 1u));
               if (edge) {
                 if (pos < 64) wq[pos] = mi;
-                else rowacc = fmaf(brightness(-buf[mi]), boundary_weight(mi), rowacc);
+                else rowacc += boundary_point(mi);
               }
               nq += __popc(msk);
             }
           }
           __syncwarp();
-          for (int q = lane; q < min(nq, 64); q += 32) {
-            int mi = wq[q];
-            rowacc = fmaf(brightness(-buf[mi]), boundary_weight(mi), rowacc);
-          }
+          for (int q = lane; q < min(nq, 64); q += 32) rowacc += boundary_point(wq[q]);
           __syncwarp();
+          if (DER) {
+            // gradient of every seeded ray's distance, recomputed from its
+            // anchor (rotated frame R = e^{-i th_m}: Q_j = R (z - a_j),
+            // u = R (f(z) - w_c) / d, gamma = sum eps_j / Q_j^2):
+            //   dd/dz = J u, J = [[1 + g.x, -g.y], [-g.y, 1 - g.x]]
+            //   dd/dr_i = (J u) . e^{i phi},  dd/dth_l = (J u) . (i z)
+            //   dd/dw_c = -conj(R) u,  dd/da_j.x = -eps_j Re(conj(u) conj(R) Q_j^2) / |Q_j|^4
+            //   dd/deps_j = -(u . Q_j) / |Q_j|^2
+            for (int m = lane; m < cnt; m += 32) {
+              const float a = ab[m];
+              if (a == 0.f) continue;
+              const int lw = wrapl(lo + m);
+              int mgrp = __float2int_rz((float)lw * igth);
+              if (mgrp * gth > lw) --mgrp;
+              else if ((mgrp + 1) * gth <= lw) ++mgrp;
+              const int o = lw - mgrp * gth;
+              const Anchor& an_ = anch[gi * mth + mgrp];
+              const cf t = tab[o];
+              const cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
+              const cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz;
+              const float n0 = abs2(Q0), n1 = abs2(Q1);
+              const float i0 = 1.0f / n0, i1 = 1.0f / n1;
+              const cf U = scl(an_.K[0] * cj(Q0), i0) + scl(an_.K[1] * cj(Q1), i1);
+              const cf pz = dz * U;
+              const cf dw = mk(an_.ws.x + dz.x + pz.x, an_.ws.y + dz.y - pz.y);
+              const float id = rsqrtf(fmaxf(abs2(dw), 1e-37f));
+              const float ux = dw.x * id, uy = dw.y * id;
+              const cf c0 = cj(Q0 * Q0), c1 = cj(Q1 * Q1);
+              const cf gm = scl(c0, sh.eps32[0] * i0 * i0) + scl(c1, sh.eps32[1] * i1 * i1);
+              const float gzx = (1.0f + gm.x) * ux - gm.y * uy;
+              const float gzy = -gm.y * ux + (1.0f - gm.x) * uy;
+              const float ex = 1.0f + t.x, ey = t.y;
+              const float gr_ = gzx * ex + gzy * ey;
+              const float gt_ = ri * (gzy * ex - gzx * ey);
+              pg[0] += a * gr_;
+              pg[1] += a * gt_;
+              pg[2] += a * gt_ * ((float)lw + 0.5f);
+              const float2 cs_ = ds.acs[gi * mth + mgrp];
+              const float ct = cs_.x, st = cs_.y;
+              pg[3] -= a * (ct * ux - st * uy);
+              pg[4] -= a * (st * ux + ct * uy);
+              // conj(R) Q_j^2 with conj(R) = (ct, st)
+              const cf P0 = mk(ct, st) * (Q0 * Q0), P1 = mk(ct, st) * (Q1 * Q1);
+              pg[7] -= a * sh.eps32[0] * (ux * P0.x + uy * P0.y) * i0 * i0;
+              pg[8] -= a * sh.eps32[1] * (ux * P1.x + uy * P1.y) * i1 * i1;
+              pg[9] -= a * (ux * Q0.x + uy * Q0.y) * i0;
+              pg[10] -= a * (ux * Q1.x + uy * Q1.y) * i1;
+            }
+            __syncwarp();
+          }
+        }
+        if (DER) {
+          // row i: S_b = sum_i K_i Row_i, K_i = r_i dr dth, r_i = r_lo + (i +
+          // 1/2) dr, dr = (r_hi - r_lo) / N_r, dth = width / N_theta
+          double v[12];
+          v[0] = (double)rowacc;
+          for (int k = 0; k < 11; ++k) v[k + 1] = (double)pg[k];
+          for (int o2 = 16; o2 > 0; o2 >>= 1)
+            for (int k = 0; k < 12; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o2);
+          const double Rw = v[0], rid = (double)ri, drd = sh.dr64, dtd = sh.dth64;
+          const double Ki = rid * drd * dtd, fi = (i + 0.5) / NR;
+          double mine = 0.0;
+          #pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            double x;
+            if (k == 0) x = Ki * v[1] * (1.0 - fi) + Rw * ((1.0 - fi) * drd * dtd - rid * dtd / NR);
+            else if (k == 1) x = Ki * v[1] * fi + Rw * (fi * drd * dtd + rid * dtd / NR);
+            else if (k == 2) x = Ki * v[2];
+            else if (k == 3) x = Ki * v[3] / NTH + Rw * rid * drd / NTH;
+            else x = Ki * v[k];
+            if (lane == k) mine = x;
+          }
+          if (lane < 12) wder[warp * 12 + lane] += mine;
         }
         // Kahan-compensated accumulation of r_i dtheta dr sum_l I W
         float term = ri * rowacc * bxw;
@@ -1264,6 +1566,12 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         acc_s = tt;
       }
       __syncthreads();
+      if (DER && tid < 12) {
+        double sum = 0.0;
+        for (int w = 0; w < NW; ++w) { sum += wder[w * 12 + tid]; wder[w * 12 + tid] = 0.0; }
+        if (tid < 4) ds.Gb[bxi][tid] = sum;
+        else ds.H[tid - 4] += sum;
+      }
     }
     if (st_local) atomicOr(&sh.status, st_local);
     if (diag_cnt && tid == 0) { long long c_ = clock64(); sh.cnt[12] = (int)min(c_ - sh.clk0, 2000000000LL); sh.clk0 = c_; }
@@ -1277,9 +1585,43 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       for (int w = 0; w < NW; ++w) tot += sh.red[w];
       double A = tot / (sh.rho * sh.rho);
       if (!(A == A) || isinf(A)) sh.status |= ICRS_ST_NAN;
-      A_out[(size_t)s * E + e] = A;
-      if (st_out) st_out[(size_t)s * E + e] = (sh.status & 0xffu) | ((uint32_t)min(sh.nbox, 255) << 8);
       size_t o = (size_t)s * E + e;
+      if (DER) {
+        // dA/dp = (sum_b G_b . d bounds_b/dp + H . d(w_c, rho, u1, a, eps)/dp) / rho^2
+        //         - 2 S / rho^3 [p = rho]
+        double dS[NPAR];
+        for (int q = 0; q < NPAR; ++q) dS[q] = 0.0;
+        for (int b = 0; b < sh.nbox; ++b)
+          for (int q = 0; q < NPAR; ++q)
+            dS[q] += ds.Gb[b][0] * bdual[b].r_lo.d[q] + ds.Gb[b][1] * bdual[b].r_hi.d[q] +
+                     ds.Gb[b][2] * bdual[b].th_lo.d[q] + ds.Gb[b][3] * bdual[b].width.d[q];
+        for (int q = 0; q < 4; ++q) dS[q] += ds.H[0] * ds.dwc[q].x + ds.H[1] * ds.dwc[q].y;
+        dS[4] += ds.H[4] * ds.dadp[0][0] + ds.H[5] * ds.dadp[1][0];
+        dS[5] += ds.H[4] * ds.dadp[0][1] + ds.H[5] * ds.dadp[1][1] + ds.H[6] * ds.depsq[0] + ds.H[7] * ds.depsq[1];
+        dS[6] += ds.H[2];
+        dS[7] += ds.H[3];
+        const double ir2 = 1.0 / (sh.rho * sh.rho);
+        double dA[NPAR];
+        for (int q = 0; q < NPAR; ++q) dA[q] = dS[q] * ir2;
+        dA[6] -= 2.0 * A / sh.rho;
+        bool bad = false;
+        for (int q = 0; q < NPAR; ++q) bad |= !(dA[q] == dA[q]) || isinf(dA[q]);
+        if (bad) sh.status |= ICRS_ST_NAN;
+        if (dout.dA)
+          for (int q = 0; q < NPAR; ++q) dout.dA[o * NPAR + q] = dA[q];
+        double wgt = 0.0;
+        if (dout.gA) wgt = dout.gA[o];
+        if (dout.yobs) {
+          // chi^2 = sum_e ((y_e - A_e) / sigma_e)^2 with the flux F = A
+          const double r_ = (dout.yobs[o] - A) / dout.sig[o];
+          wgt = -2.0 * r_ / dout.sig[o];
+          if (dout.chi2) atomicAdd(&dout.chi2[s], r_ * r_);
+        }
+        if (dout.grad)
+          for (int q = 0; q < NPAR; ++q) atomicAdd(&dout.grad[(size_t)s * NPAR + q], wgt * dA[q]);
+      }
+      if (A_out) A_out[o] = A;
+      if (st_out) st_out[o] = (sh.status & 0xffu) | ((uint32_t)min(sh.nbox, 255) << 8);
       if (diag_cnt)
         for (int c = 0; c < 16; ++c) diag_cnt[o * 16 + c] = sh.cnt[c];
       if (diag_sect)
@@ -1401,15 +1743,20 @@ __global__ void point_source_kernel(const icrs_params* __restrict__ P, int S, co
 }
 
 // ---------------------------------------------------------------- host side
-static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax) {
+static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, bool der) {
   const int N = NL * NL + 1;
   const size_t NP = (size_t)g.n_limb * N;
-  size_t b = 0;
+  size_t b = has_plo ? sizeof(cf) * NP : 0;
   b += sizeof(cf) * NP + 4 * sizeof(float) * NP;
   b += sizeof(short) * ((NP + 7) & ~(size_t)7);
   b += 3 * ((NP + 15) & ~(size_t)15);
   b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
   b += sizeof(int) * NW * 64;  // per-warp boundary queues
+  if (der) {
+    b += sizeof(DerShared);
+    const int seg2 = g.n_theta < 1024 ? g.n_theta : 1024;
+    b += sizeof(float) * NW * (seg2 + 4);
+  }
   b += sizeof(cf) * g.n_theta;
   const int seg = g.n_theta < 1024 ? g.n_theta : 1024;
   b += sizeof(float) * NW * (seg + 4);
@@ -1441,6 +1788,77 @@ static int first_n_lens(const icrs_params* p, cudaStream_t st, int* nl) {
   if (v != 2 && v != 3) return ICRS_EINVAL;
   *nl = v;
   return ICRS_OK;
+}
+
+// Launch of one instantiation: shared-memory sizing (the FP64 point table
+// takes what is left, up to 2048 entries), occupancy, contiguous chunks of
+// epochs per block (warm starts along the light curve).
+template <int NL, bool DER>
+static int launch_inst(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, double* A,
+                       uint32_t* status, double* dsect, int32_t* dcnt, float* dpts, const DerOut& dout,
+                       cudaStream_t st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ICRS_ECUDA;
+  int optin = 0, nsm = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return ICRS_ECUDA;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ICRS_ECUDA;
+  int pmax = PMAX_MIN;
+  int has_plo = 1;  // keep the lo part of image positions when it fits
+  if (mag_smem_bytes(NL, *g, pmax, has_plo, DER) + sizeof(Shared) > (size_t)optin) has_plo = 0;
+  size_t smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER);
+  if (smem + sizeof(Shared) > (size_t)optin) return ICRS_EUNSUPPORTED;
+  while (pmax < 2048 && mag_smem_bytes(NL, *g, pmax * 2, has_plo, DER) + sizeof(Shared) <= (size_t)optin) pmax *= 2;
+  smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER);
+  if (cudaFuncSetAttribute(mag_kernel<NL, DER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return ICRS_ECUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mag_kernel<NL, DER>, NT, smem) != cudaSuccess) return ICRS_ECUDA;
+  if (per_sm < 1) return ICRS_EUNSUPPORTED;
+  long long tiles = (long long)S * E;
+  long long slots = (long long)nsm * per_sm;
+  long long per_block = (tiles + slots - 1) / slots;
+  if (per_block < 1) per_block = 1;
+  long long blocks = (tiles + per_block - 1) / per_block;
+  mag_kernel<NL, DER><<<(unsigned)blocks, NT, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect, dcnt,
+                                                          dpts, pmax, has_plo, dout);
+  return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
+}
+
+static int launch_mag(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g,
+                      double* A, uint32_t* status, double* dsect, int32_t* dcnt, float* dpts, void* stream) {
+  if (S < 0 || E < 0) return ICRS_EINVAL;
+  if (S == 0 || E == 0) return check_grid(g);
+  if (!p || !t || !A) return ICRS_EINVAL;
+  int rc = check_grid(g);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int nl = g->n_lens;
+  if (nl == 0) { rc = first_n_lens(p, st, &nl); if (rc) return rc; }
+  if (nl != 2 && nl != 3) return ICRS_EINVAL;
+  DerOut none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (nl == 2) return launch_inst<2, false>(p, S, t, E, g, A, status, dsect, dcnt, dpts, none, st);
+  return launch_inst<3, false>(p, S, t, E, g, A, status, dsect, dcnt, dpts, none, st);
+}
+
+// Derivative launch (binary lens only): zeroes the accumulated outputs on the
+// stream, then runs the derivative instantiation.
+static int launch_der(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, DerOut d,
+                      double* A, uint32_t* status, void* stream) {
+  if (S < 0 || E < 0) return ICRS_EINVAL;
+  int rc = check_grid(g);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (S > 0) {
+    if (d.grad && cudaMemsetAsync(d.grad, 0, sizeof(double) * NPAR * (size_t)S, st) != cudaSuccess) return ICRS_ECUDA;
+    if (d.chi2 && cudaMemsetAsync(d.chi2, 0, sizeof(double) * (size_t)S, st) != cudaSuccess) return ICRS_ECUDA;
+  }
+  if (S == 0 || E == 0) return ICRS_OK;
+  if (!p || !t) return ICRS_EINVAL;
+  int nl = g->n_lens;
+  if (nl == 0) { rc = first_n_lens(p, st, &nl); if (rc) return rc; }
+  if (nl == 3) return ICRS_EUNSUPPORTED;
+  if (nl != 2) return ICRS_EINVAL;
+  return launch_inst<2, true>(p, S, t, E, g, A, status, nullptr, nullptr, nullptr, d, st);
 }
 
 }  // namespace icrs
@@ -1491,49 +1909,6 @@ int icrs_point_source(const icrs_params* p, int S, const double* w, int n, const
   return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
 }
 
-static int launch_mag(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g,
-                      double* A, uint32_t* status, double* dsect, int32_t* dcnt, float* dpts, void* stream) {
-  if (S < 0 || E < 0) return ICRS_EINVAL;
-  if (S == 0 || E == 0) return check_grid(g);
-  if (!p || !t || !A) return ICRS_EINVAL;
-  int rc = check_grid(g);
-  if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
-  int nl = g->n_lens;
-  if (nl == 0) { rc = first_n_lens(p, st, &nl); if (rc) return rc; }
-  if (nl != 2 && nl != 3) return ICRS_EINVAL;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return ICRS_ECUDA;
-  int optin = 0, nsm = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  // the FP64 table takes whatever shared memory is left (up to 4096 entries)
-  int pmax = PMAX_MIN;
-  size_t smem = mag_smem_bytes(nl, *g, pmax);
-  if (smem + sizeof(Shared) > (size_t)optin) return ICRS_EUNSUPPORTED;
-  while (pmax < 4096 && mag_smem_bytes(nl, *g, pmax * 2) + sizeof(Shared) <= (size_t)optin) pmax *= 2;
-  smem = mag_smem_bytes(nl, *g, pmax);
-  cudaError_t ce;
-  if (nl == 2) ce = cudaFuncSetAttribute(mag_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  else ce = cudaFuncSetAttribute(mag_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (ce != cudaSuccess) return ICRS_ECUDA;
-  int per_sm = 0;
-  if (nl == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mag_kernel<2>, NT, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mag_kernel<3>, NT, smem);
-  if (per_sm < 1) return ICRS_EUNSUPPORTED;
-  long long tiles = (long long)S * E;
-  long long slots = (long long)nsm * per_sm;
-  // contiguous chunks of epochs per block (warm starts along the light curve)
-  long long per_block = (tiles + slots - 1) / slots;
-  if (per_block < 1) per_block = 1;
-  long long blocks = (tiles + per_block - 1) / per_block;
-  if (nl == 2)
-    mag_kernel<2><<<(unsigned)blocks, NT, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect, dcnt, dpts, pmax);
-  else
-    mag_kernel<3><<<(unsigned)blocks, NT, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect, dcnt, dpts, pmax);
-  return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
-}
-
 int icrs_magnification(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g,
                        double* A, uint32_t* status, void* stream) {
   return launch_mag(p, S, t, E, g, A, status, nullptr, nullptr, nullptr, stream);
@@ -1543,6 +1918,22 @@ int icrs_magnification_diag(const icrs_params* p, int S, const double* t, int E,
                             double* A, uint32_t* status, double* sectors, int32_t* counters,
                             float* points, void* stream) {
   return launch_mag(p, S, t, E, g, A, status, sectors, counters, points, stream);
+}
+
+int icrs_magnification_vjp(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g,
+                           const double* gA, double* grad, double* dA, double* A, uint32_t* status, void* stream) {
+  if (S > 0 && E > 0 && !gA && grad) return ICRS_EINVAL;
+  if (S > 0 && !grad && !dA) return ICRS_EINVAL;
+  DerOut d = {gA, nullptr, nullptr, dA, grad, nullptr};
+  return launch_der(p, S, t, E, g, d, A, status, stream);
+}
+
+int icrs_chi2_grad(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, const double* y,
+                   const double* sigma, double* chi2, double* grad, double* A, uint32_t* status, void* stream) {
+  if (S > 0 && E > 0 && (!y || !sigma)) return ICRS_EINVAL;
+  if (S > 0 && (!chi2 || !grad)) return ICRS_EINVAL;
+  DerOut d = {nullptr, y, sigma, nullptr, grad, chi2};
+  return launch_der(p, S, t, E, g, d, A, status, stream);
 }
 
 }  // extern "C"

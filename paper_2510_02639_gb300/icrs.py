@@ -20,7 +20,11 @@ ST_NONCONV, ST_IMGCOUNT, ST_SECTCAP, ST_EDGE, ST_NAN, ST_OVERFLOW = 1, 2, 4, 8, 
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = ("icrs_grid_default", "icrs_point_source", "icrs_magnification",
-            "icrs_magnification_diag", "icrs_strerror", "icrs_abi_version")
+            "icrs_magnification_diag", "icrs_magnification_vjp", "icrs_chi2_grad",
+            "icrs_strerror", "icrs_abi_version")
+
+# Order of the 8 derivative slots of icrs_magnification_vjp / icrs_chi2_grad.
+PARAM_ORDER = ("t0", "tE", "u0", "alpha", "s", "q", "rho", "u1")
 
 
 class IcrsParams(ctypes.Structure):
@@ -67,6 +71,12 @@ def _load():
     L.icrs_magnification_diag.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid),
                                           vp, vp, vp, vp, vp, vp]
     L.icrs_magnification_diag.restype = ctypes.c_int
+    L.icrs_magnification_vjp.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid),
+                                         vp, vp, vp, vp, vp, vp]
+    L.icrs_magnification_vjp.restype = ctypes.c_int
+    L.icrs_chi2_grad.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid),
+                                 vp, vp, vp, vp, vp, vp, vp]
+    L.icrs_chi2_grad.restype = ctypes.c_int
     L.icrs_strerror.argtypes = [ctypes.c_int]
     L.icrs_strerror.restype = ctypes.c_char_p
     L.icrs_abi_version.restype = ctypes.c_int
@@ -171,3 +181,92 @@ def grid_from_dict(d: dict, n_lens: int = 2) -> IcrsGrid:
                      max_iter=int(d["max_iter"]), uniform=int(d["uniform"]), n_lens=int(n_lens),
                      delta_c=float(d["delta_c"]), margin=float(d["margin"]),
                      img_tol=float(d["img_tol"]))
+
+
+def magnification_vjp(params_dev, t, grid: IcrsGrid, gA, per_epoch=False, stream=None):
+    """Binary lens.  grad[s] = sum_e gA[s, e] dA[s, e]/dp over the 8 parameters
+    of PARAM_ORDER.  Returns (grad [S, 8], dA [S, E, 8] or None, A [S, E],
+    status [S, E])."""
+    import torch
+    S = params_dev.numel() // PARAMS_DTYPE.itemsize
+    E = t.shape[-1]
+    assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    assert gA.dtype == torch.float64 and gA.is_contiguous() and tuple(gA.shape) == (S, E)
+    grad = torch.empty((S, 8), dtype=torch.float64, device=t.device)
+    dA = torch.empty((S, E, 8), dtype=torch.float64, device=t.device) if per_epoch else None
+    A = torch.empty((S, E), dtype=torch.float64, device=t.device)
+    st = torch.empty((S, E), dtype=torch.int32, device=t.device)
+    check(lib.icrs_magnification_vjp(_ptr(params_dev), S, _ptr(t), E, ctypes.byref(grid), _ptr(gA),
+                                     _ptr(grad), _ptr(dA), _ptr(A), _ptr(st), _stream(torch, stream)))
+    return grad, dA, A, st
+
+
+def chi2_grad(params_dev, t, grid: IcrsGrid, y, sigma, stream=None):
+    """chi^2 = sum_e ((y - A) / sigma)^2 per set and its gradient over the 8
+    parameters of PARAM_ORDER.  Returns (chi2 [S], grad [S, 8], A [S, E],
+    status [S, E])."""
+    import torch
+    S = params_dev.numel() // PARAMS_DTYPE.itemsize
+    E = t.shape[-1]
+    for x in (t, y, sigma):
+        assert x.dtype == torch.float64 and x.is_cuda and x.is_contiguous() and tuple(x.shape) == (S, E)
+    chi2 = torch.empty((S,), dtype=torch.float64, device=t.device)
+    grad = torch.empty((S, 8), dtype=torch.float64, device=t.device)
+    A = torch.empty((S, E), dtype=torch.float64, device=t.device)
+    st = torch.empty((S, E), dtype=torch.int32, device=t.device)
+    check(lib.icrs_chi2_grad(_ptr(params_dev), S, _ptr(t), E, ctypes.byref(grid), _ptr(y), _ptr(sigma),
+                             _ptr(chi2), _ptr(grad), _ptr(A), _ptr(st), _stream(torch, stream)))
+    return chi2, grad, A, st
+
+
+def pack_binary(theta):
+    """Device-side packing of binary-lens parameters theta [S, 8] (PARAM_ORDER,
+    float64) into icrs_params structs (uint8 tensor)."""
+    import torch
+    S = theta.shape[0]
+    buf = torch.zeros((S, PARAMS_DTYPE.itemsize // 8), dtype=torch.float64, device=theta.device)
+    th = theta.detach()
+    # struct order: t0, tE, u0, alpha, rho, u1, (n_lens, reserved), s, q, ...
+    for dst, src in ((0, 0), (1, 1), (2, 2), (3, 3), (4, 6), (5, 7), (7, 4), (8, 5)):
+        buf[:, dst] = th[:, src]
+    buf.view(torch.int32)[:, 12] = 2
+    return buf.view(torch.uint8).reshape(-1)
+
+
+def _autograd_function():
+    import torch
+
+    class Magnification(torch.autograd.Function):
+        """A [S, E] = ICRS magnification of binary-lens parameters theta [S, 8]
+        (PARAM_ORDER) at epochs t [S, E].  Backward: icrs_magnification_vjp,
+        which recomputes the rays of every epoch."""
+
+        @staticmethod
+        def forward(ctx, theta, t, grid):
+            pd = pack_binary(theta)
+            A, st = magnification(pd, t, grid)
+            ctx.save_for_backward(t)
+            ctx.pd = pd
+            ctx.grid = grid
+            ctx.status = st
+            return A
+
+        @staticmethod
+        def backward(ctx, gA):
+            (t,) = ctx.saved_tensors
+            grad, _, _, _ = magnification_vjp(ctx.pd, t, ctx.grid, gA.contiguous().to(torch.float64))
+            return grad, None, None
+
+    return Magnification
+
+
+_MAG_FN = None
+
+
+def magnification_ad(theta, t, grid: IcrsGrid):
+    """Differentiable magnification (torch.autograd): theta [S, 8] float64 on
+    the device in PARAM_ORDER, t [S, E] float64.  Binary lens."""
+    global _MAG_FN
+    if _MAG_FN is None:
+        _MAG_FN = _autograd_function()
+    return _MAG_FN.apply(theta, t, grid)

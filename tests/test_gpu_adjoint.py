@@ -1,0 +1,190 @@
+"""GPU parity of the adjoint (icrs_magnification_vjp, icrs_chi2_grad, the
+autograd Function) against the oracle's FP64 forward-mode derivative and
+against central finite differences of the oracle's FP64 magnification.
+
+Tolerance.  The rays and their tangents run in FP32.  Each per-ray tangent
+carries a relative rounding error of a few 1e-7.  So does its seed, the
+derivative of the brightness and of the crossing weights.  Two sums lose more
+than that:
+  - the sector-bound terms, dS/d(r_lo, r_hi, th_lo, width);
+  - the radial terms, which nearly cancel: moving a bound shifts every ray.
+The bound is therefore set per component p:
+  |dA_gpu - dA_oracle| <= RTOL |dA_oracle| + ATOL * max_e |dA_oracle[:, p]|,
+with RTOL = 2e-3 and ATOL = 5e-4 of the largest value of that component over
+the light curve.  The boundary crossings and their slopes are taken in FP64.
+What remains is the FP32 error of the interior ray distances.  That error is
+about 1e-7 of the ray's offset from its anchor, and it enters the cancelling
+sums at about 1e-6 A / rho per unit source-plane shift.  At the peak of a
+light curve this is ~1e-4 of max |dA/dp|.  dA/du1 is the difference of two nearly equal flux integrals
+(the limb-darkening law keeps the total flux fixed).  Its absolute error
+follows the forward error of A, so it gets the floor TAU * A, where TAU = 1e-5
+is the forward parity tolerance.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_02639_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 2e-3
+ATOL = 5e-4
+TAU = 1e-5
+NAMES = ("t0", "tE", "u0", "alpha", "s", "q", "rho", "u1")
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_02639_gb300 import build as B
+    B.build()
+    from paper_2510_02639_gb300 import icrs
+    return icrs
+
+
+def gpu_dA(icrs, params, t, grid):
+    import torch
+    pd = icrs.params_to_device(params)
+    tt = torch.tensor(np.asarray(t, dtype=np.float64).reshape(len(params), -1), device="cuda")
+    gA = torch.ones_like(tt)
+    grad, dA, A, st = icrs.magnification_vjp(pd, tt, icrs.grid_from_dict(grid, 2), gA, per_epoch=True)
+    torch.cuda.synchronize()
+    return A.cpu().numpy(), dA.cpu().numpy(), st.cpu().numpy(), grad.cpu().numpy()
+
+
+def bound_of(dAo, Ao):
+    S, E, P = dAo.shape
+    scale = np.abs(dAo).reshape(S * E, P).max(axis=0)
+    bound = RTOL * np.abs(dAo) + ATOL * scale
+    bound[..., 7] += TAU * Ao
+    return bound
+
+
+def assert_dA(dA, dAo, what, Ao):
+    S, E, P = dAo.shape
+    err = np.abs(dA - dAo)
+    bound = bound_of(dAo, Ao)
+    ratio = err / np.maximum(bound, 1e-300)
+    worst = [f"{NAMES[p]}:{ratio[..., p].max():.2f}" for p in range(P)]
+    print(what, "worst err/bound per parameter", " ".join(worst))
+    assert np.all(np.isfinite(dA)), what
+    assert np.all(ratio <= 1.0), f"{what}: {np.sum(ratio > 1)} of {ratio.size} above; {worst}"
+
+
+def test_dA_caustic_crossing(G, oracle_mod):
+    """The caustic-crossing light curve (s=1, q=1e-3, rho=1e-3): 42 of its
+    500 epochs, crossings included."""
+    params, t = I.caustic_crossing_binary()
+    t = t[:, ::12]
+    g = I.grid()
+    A, dA, st, _ = gpu_dA(G, params, t, g)
+    Ao, dAo, so = oracle_mod.magnification_fwd(params, t, g)
+    assert np.all(np.abs(A / Ao - 1) <= 1e-5)
+    assert_dA(dA, dAo, "caustic", Ao)
+
+
+def test_dA_adjoint_sets(G, oracle_mod):
+    """Three sets of the 256-set adjoint batch (q ~ 1e-4, rho ~ 8e-4), epochs
+    concentrated around the closest approach, plus a ragged tail."""
+    params, t, _, _ = I.adjoint_batch(n_sets=3, n_epochs=37)
+    rng = np.random.default_rng(5)
+    t = np.stack([np.sort(np.concatenate([rng.uniform(-1.5, 1.5, 30), rng.uniform(-50, 50, 7)])) for _ in range(3)])
+    g = I.grid()
+    A, dA, st, _ = gpu_dA(G, params, t, g)
+    Ao, dAo, so = oracle_mod.magnification_fwd(params, t, g)
+    assert np.all(np.abs(A / Ao - 1) <= 1e-5)
+    assert_dA(dA, dAo, "adjoint sets", Ao)
+
+
+def test_dA_uniform_and_grid_variants(G, oracle_mod):
+    params, t = I.caustic_crossing_binary(n_epochs=40)
+    t = t[:, ::2]
+    for g in (I.grid(uniform=1), I.grid(n_r=37, n_theta=500)):
+        A, dA, st, _ = gpu_dA(G, params, t, g)
+        Ao, dAo, so = oracle_mod.magnification_fwd(params, t, g)
+        assert_dA(dA, dAo, str(g), Ao)
+
+
+def test_vjp_and_chi2_against_oracle(G, oracle_mod):
+    """grad = sum_e gA_e dA_e for a random upstream gA; chi^2 and its gradient
+    against the oracle's A and dA."""
+    import torch
+    params, t, centre, noise = I.adjoint_batch(n_sets=2, n_epochs=24)
+    t = np.stack([np.linspace(-1.0, 1.0, 24)] * 2)
+    g = I.grid()
+    Ao, dAo, _ = oracle_mod.magnification_fwd(params, t, g)
+    Ac, _ = oracle_mod.magnification([centre] * 2, t, g)
+    y = Ac + noise[:, :24]
+    sig = np.full_like(y, 0.01)
+    pd = G.params_to_device(params)
+    tt = torch.tensor(t, device="cuda")
+    rng = np.random.default_rng(3)
+    gA = rng.standard_normal(t.shape)
+    grad, dA, A, st = G.magnification_vjp(pd, tt, G.grid_from_dict(g, 2), torch.tensor(gA, device="cuda"), per_epoch=True)
+    grad = grad.cpu().numpy(); dA = dA.cpu().numpy()
+    np.testing.assert_allclose(grad, np.einsum("se,sep->sp", gA, dA), rtol=1e-9, atol=1e-12 * np.abs(dA).max())
+    chi2, cgrad, A2, st2 = G.chi2_grad(pd, tt, G.grid_from_dict(g, 2), torch.tensor(y, device="cuda"),
+                                       torch.tensor(sig, device="cuda"))
+    chi2 = chi2.cpu().numpy(); cgrad = cgrad.cpu().numpy()
+    r = (y - Ao) / sig
+    chi2_o = (r * r).sum(axis=1)
+    grad_o = np.einsum("se,sep->sp", -2.0 * r / sig, dAo)
+    np.testing.assert_allclose(chi2, chi2_o, rtol=1e-3)
+    scale = np.abs(np.einsum("se,sep->sep", -2.0 * r / sig, dAo)).sum(axis=1)
+    assert np.all(np.abs(cgrad - grad_o) <= RTOL * scale + 1e-12), (cgrad, grad_o)
+
+
+def test_dA_against_central_differences(G, oracle_mod):
+    """Central differences of the oracle's FP64 magnification, h = 1e-6
+    (relative for tE, s, q, rho; absolute for t0, u0, alpha, u1).  Components
+    where a step flips a discrete decision (the oracle's own forward-mode
+    derivative and its difference quotient disagree) are skipped."""
+    p = I.binary(s=1.0, q=1e-3, rho=1e-3, u1=0.5, u0=0.01, alpha=0.5, t0=0.0, tE=20.0)
+    t = np.array([-0.31, -0.12, 0.05, 0.22, 0.4])
+    g = I.grid()
+    A, dA, st, _ = gpu_dA(G, [p], t, g)
+    Ao, dAo, _ = oracle_mod.magnification_fwd([p], t, g)
+    bound = bound_of(dAo, Ao)
+    checked = 0
+    for k, name in enumerate(NAMES):
+        rel = name in ("tE", "s", "q", "rho")
+        h = 1e-6 * (p[name] if rel else 1.0)
+        pp, pm = dict(p), dict(p)
+        pp[name] += h; pm[name] -= h
+        fd = (oracle_mod.magnification([pp], t, g)[0] - oracle_mod.magnification([pm], t, g)[0])[0] / (2 * h)
+        for e in range(len(t)):
+            # FP64 rounding of the quotient is ~1e-16 A / h; a larger gap to
+            # the oracle's own derivative means a decision flipped in the step
+            if abs(fd[e] - dAo[0, e, k]) > 1e-4 * abs(dAo[0, e, k]) + 1e-9 * Ao[0, e] / h:
+                continue
+            checked += 1
+            assert abs(dA[0, e, k] - fd[e]) <= bound[0, e, k], (name, e, dA[0, e, k], fd[e])
+    assert checked >= 20
+
+
+def test_autograd_function(G):
+    import torch
+    params, t, _, _ = I.adjoint_batch(n_sets=2, n_epochs=8)
+    theta = torch.tensor(I.param_matrix(params), device="cuda", requires_grad=True)
+    tt = torch.tensor(np.stack([np.linspace(-0.8, 0.8, 8)] * 2), device="cuda")
+    g = G.make_grid()
+    A = G.magnification_ad(theta, tt, g)
+    w = torch.linspace(0.5, 1.5, 8, device="cuda", dtype=torch.float64).expand(2, 8)
+    (A * w).sum().backward()
+    ref, _, A2, _ = G.magnification_vjp(G.params_to_device(params), tt, g, w.contiguous())
+    torch.testing.assert_close(A, A2, rtol=1e-6, atol=0)
+    torch.testing.assert_close(theta.grad, ref, rtol=1e-9, atol=0)
+
+
+def test_unsupported_and_empty(G):
+    import torch
+    pd = G.params_to_device([I.triple()])
+    t = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(G.IcrsError):
+        G.magnification_vjp(pd, t, G.make_grid(n_lens=3), torch.ones_like(t))
+    pd = G.params_to_device([I.binary()])
+    t = torch.zeros((1, 0), dtype=torch.float64, device="cuda")
+    grad, dA, A, st = G.magnification_vjp(pd, t, G.make_grid(), torch.zeros_like(t))
+    assert torch.all(grad == 0)
