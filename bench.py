@@ -8,6 +8,12 @@ whole batch (one fused kernel launch).  Inputs are resident in HBM; the L2 is
 flushed (a 256 MiB write) between timed steps and each step is timed with CUDA
 events on the launching stream.
 
+The same line carries "chi2_grad": chi^2 gradient evaluations per second
+(one unit = one parameter set's gradient over its 5,000-epoch light curve,
+8 parameters) on the adjoint batch, 256 sets around s=0.9, q=1e-4,
+rho=8e-4, each perturbed by 1%.  One call of icrs_chi2_grad does the whole
+batch, timed like the magnification steps.
+
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the baseline arm).
 
@@ -159,6 +165,37 @@ def cpu_baseline(params, t, g, seconds=12.0):
             "sample": f"{n} random (set, epoch) pairs of the workload, FP64 single thread, {dt:.1f} s"}
 
 
+def chi2_bench(icrs, I, args, dev, stream, flush, n_sets):
+    """Timed icrs_chi2_grad steps over the adjoint batch (first n_sets sets)."""
+    import torch
+    params, t, centre, noise = I.adjoint_batch()
+    params, t, noise = params[:n_sets], t[:n_sets], noise[:n_sets]
+    g = icrs.grid_from_dict(I.grid(), 2)
+    pd = icrs.params_to_device(params, dev)
+    tt = torch.tensor(t, dtype=torch.float64, device=dev)
+    # data: magnification of the centre parameters plus Gaussian noise (F = A)
+    Ac, _ = icrs.magnification(icrs.params_to_device([centre] * len(params), dev), tt, g)
+    y = (Ac + torch.tensor(noise, device=dev)).contiguous()
+    sig = torch.full_like(y, 0.01)
+    for _ in range(args.warmup):
+        icrs.chi2_grad(pd, tt, g, y, sig, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        chi2, grad, A, st = icrs.chi2_grad(pd, tt, g, y, sig, stream=stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    sec = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
+    ok = bool(torch.isfinite(grad).all().item())
+    return {"value": len(params) * args.steps / sec, "unit": "chi^2 gradients/s",
+            "epochs_per_s": len(params) * t.shape[1] * args.steps / sec,
+            "ms_per_step": sec / args.steps * 1e3, "steps": args.steps, "warmup": args.warmup,
+            "workload": f"adjoint_batch_{len(params)}x{t.shape[1]}", "params": 8, "dtype": "f32",
+            "finite": ok, "gpu_launches": args.steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -168,6 +205,7 @@ def main():
     ap.add_argument("--workload", default="batch", choices=["batch", "caustic", "triple"])
     ap.add_argument("--ref-sample", type=int, default=400)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chi2-sets", type=int, default=256, help="sets of the adjoint batch per chi^2 step (0: skip)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -270,6 +308,8 @@ def main():
                "h2d_bytes_per_step": int(h_params.numel() + h_t.numel() * 8),
                "d2h_bytes_per_step": int(h_A.numel() * 8 + h_st.numel() * 4)}
 
+    chi2 = chi2_bench(icrs, I, args, dev, stream, flush, args.chi2_sets) if args.chi2_sets > 0 else None
+
     clocks = clk.summary() if rank == 0 else None
     if rank != 0:
         return
@@ -289,6 +329,7 @@ def main():
                              f"over the fused kernel's event time; peak = 152 SM x 128 FP32 lanes x 2 x max SM clock"},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "chi2_grad": chi2,
         "clocks": clocks,
         "gpu_launches": args.steps,
         "status_flags": {k: int(np.count_nonzero(stc & b)) for k, b in

@@ -44,8 +44,8 @@ constexpr int MAXRB = 32;        // r bins per theta run
 constexpr int MAXCELL = 96;      // (theta run, r run) cells
 constexpr int MAXBOX = 96;       // candidate sectors before merging
 constexpr int MAXANCH = 128;     // FP64 anchors per sector
-constexpr int MAXCELL_D = 40;    // cells with tracked derivatives
-constexpr int MAXBOX_D = 40;     // candidate sectors with tracked derivatives
+constexpr int MAXCELL_D = 32;    // cells with tracked derivatives
+constexpr int MAXBOX_D = 32;     // candidate sectors with tracked derivatives
 constexpr float TINY_EXTENT = 3e-4f;  // images smaller than this x rho skip FP64 decisions
 constexpr float EPS32 = 5.9604645e-8f;  // 2^-24
 
@@ -124,6 +124,7 @@ struct DerShared {
   DualD cx[MAXCELL_D * 4];  // cell extremes with tangents
   BoxT<DualD> box[MAXBOX_D];  // sectors with tangents
   double wder[NW][12];      // per-warp sums of the row derivatives
+  double bdist[NW][6][5];   // FP64 stencil distances of up to 6 boundary points per warp
   float2 acs[MAXANCH];      // cos, sin of each anchor angle
 };
 
@@ -401,7 +402,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   int* queue = (int*)p;          p += sizeof(int) * QMAX;
   Anchor* anch = (Anchor*)p;     p += sizeof(Anchor) * MAXANCH;
   cf* tab = (cf*)p;              p += sizeof(cf) * g.n_theta;
-  const int seg = g.n_theta < 1024 ? g.n_theta : 1024;
+  const int segmax = DER ? 512 : 1024;  // rays per row segment
+  const int seg = g.n_theta < segmax ? g.n_theta : segmax;
   float* rowbuf = (float*)p;     p += sizeof(float) * NW * (seg + 4);
   cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
   int* wqueue = (int*)p;         p += sizeof(int) * NW * 64;  // boundary points of the current row
@@ -1337,7 +1339,9 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           // and the crossing are taken in FP64 in this mode.
           float sd_c[2], sd_l[2][4];
           int sd_b[2], sd_n[2];
-          auto boundary_weight = [&](int mi) -> float {
+          // dist (derivative mode): FP64 distances of rays mi-2 .. mi+2 (inf
+          // beyond a non-periodic edge), or NULL to compute them here
+          auto boundary_weight = [&](int mi, const double* dist) -> float {
             float d2 = -buf[mi];
             float vl = buf[mi - 1], vr = buf[mi + 1];
             bool Lin = signbit(vl), Rin = signbit(vr);
@@ -1353,29 +1357,60 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                   delta = 0.5f;
                   st_local |= ICRS_ST_EDGE;
                 } else if (DER) {
+                  // FP64 stencil; FP32 regula falsi, then Newton on the FP64
+                  // cubic; f, f' and the basis in FP32 at the FP64 crossing
                   const int c0 = isL ? -2 : -1;
-                  const int l = lo + mi;
-                  double xsd[4], ysd[4], l64[4];
+                  double xsd[4], ysd[4];
+                  float ysf[4];
                   int nd = 0;
                   double yin = 0, yout = 0;
                   for (int c = 0; c < 4; ++c) {
-                    int ll2 = l + c0 + c;
-                    if (!B.periodic && (ll2 < 0 || ll2 >= NTH)) { st_local |= ICRS_ST_EDGE; continue; }
-                    int lw2 = ((ll2 % NTH) + NTH) % NTH;
-                    xsd[nd] = (double)(c0 + c);
-                    ysd[nd] = ray_distance64<NL>(sh, B, i, lw2);
-                    if (c0 + c == 0) yin = ysd[nd];
-                    if (c0 + c == (isL ? -1 : 1)) yout = ysd[nd];
+                    const int off = c0 + c;
+                    double v;
+                    if (dist) {
+                      v = dist[off + 2];
+                    } else {
+                      const int l2_ = lo + mi + off;
+                      v = (!B.periodic && (l2_ < 0 || l2_ >= NTH)) ? __longlong_as_double(0x7ff0000000000000LL)
+                                                                   : ray_distance64<NL>(sh, B, i, wrapl(l2_));
+                    }
+                    if (isinf(v)) { st_local |= ICRS_ST_EDGE; continue; }
+                    xsd[nd] = (double)off;
+                    ysd[nd] = v;
+                    ysf[nd] = (float)v;
+                    if (off == 0) yin = v;
+                    if (off == (isL ? -1 : 1)) yout = v;
                     ++nd;
                   }
-                  double xd = crossing_solve<double>(ysd, xsd[0], nd, yin, yout, isL ? -1.0 : 1.0, sh.rho, 1e-14, 60);
-                  double dd = isL ? -xd : xd;
-                  float fv = (float)fdelta<double>(dd, g.delta_c, g.uniform);
+                  const double dd1 = ysd[1] - ysd[0];
+                  const double dd2 = nd > 2 ? 0.5 * (ysd[2] - 2.0 * ysd[1] + ysd[0]) : 0.0;
+                  const double dd3 = nd > 3 ? (ysd[3] - 3.0 * ysd[2] + 3.0 * ysd[1] - ysd[0]) * (1.0 / 6.0) : 0.0;
+                  double xd = crossing_solve<float>(ysf, (float)xsd[0], nd, (float)yin, (float)yout, isL ? -1.0f : 1.0f,
+                                                    rho32, 1e-5f, 12);
+                  bool ok = true;
+                  for (int it = 0; it < 2; ++it) {
+                    const double tt = xd - xsd[0];
+                    const double pv = ysd[0] + tt * (dd1 + (tt - 1.0) * (dd2 + (tt - 2.0) * dd3)) - sh.rho;
+                    const double pd = dd1 + (2.0 * tt - 1.0) * dd2 + ((3.0 * tt - 6.0) * tt + 2.0) * dd3;
+                    if (!(pd != 0.0)) { ok = false; break; }
+                    xd -= pv / pd;
+                  }
+                  if (!ok || !(isL ? (xd >= -1.0 && xd <= 0.0) : (xd >= 0.0 && xd <= 1.0)))
+                    xd = crossing_solve<double>(ysd, xsd[0], nd, yin, yout, isL ? -1.0 : 1.0, sh.rho, 1e-14, 60);
+                  const double dd = isL ? -xd : xd;
+                  const float dl = (float)dd;
+                  float fv, fp;
+                  if (g.uniform) { fv = dl + 0.5f; fp = 1.0f; }
+                  else if (dd >= g.delta_c) {
+                    const float sq = sqrtf(1.0f + 0.5f / dl);
+                    fv = (0.5f + dl) * (2.0f / 3.0f) * sq;
+                    fp = (2.0f / 3.0f) * sq - (0.5f + dl) / (6.0f * dl * dl * sq);
+                  } else { fv = (2.0f / 3.0f) * dl + 0.5f; fp = 2.0f / 3.0f; }
                   if (isL) fL = fv; else fR = fv;
-                  double slope = lagrange_basis<double>(ysd, nd, xd - xsd[0], l64);
-                  double fp = fdelta_prime<double>(dd, g.delta_c, g.uniform);
+                  const double tt = xd - xsd[0];
+                  const double slope = dd1 + (2.0 * tt - 1.0) * dd2 + ((3.0 * tt - 6.0) * tt + 2.0) * dd3;
+                  (void)lagrange_basis<float>(ysf, nd, (float)tt, sd_l[side]);
                   sd_c[side] = (float)((isL ? -fp : fp) / slope);
-                  for (int m = 0; m < nd; ++m) sd_l[side][m] = (float)l64[m];
                   sd_b[side] = mi + (int)xsd[0];
                   sd_n[side] = nd;
                   continue;
@@ -1430,11 +1465,11 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             return W;
           };
           // contribution I W of boundary point mi; derivative mode: its seeds
-          auto boundary_point = [&](int mi) -> float {
-            if (!DER) return brightness(-buf[mi]) * boundary_weight(mi);
+          auto boundary_point = [&](int mi, const double* dist) -> float {
+            if (!DER) return brightness(-buf[mi]) * boundary_weight(mi, dist);
             float Id, Ir, Iu;
             float I = brightness_der(-buf[mi], &Id, &Ir, &Iu);
-            float W = boundary_weight(mi);
+            float W = boundary_weight(mi, dist);
             atomicAdd(&ab[mi], W * Id);
             pg[5] += W * Ir;
             pg[6] += W * Iu;
@@ -1476,13 +1511,31 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               int pos = nq + __popc(msk & ((1u << lane) - 1u));
               if (edge) {
                 if (pos < 64) wq[pos] = mi;
-                else rowacc += boundary_point(mi);
+                else rowacc += boundary_point(mi, nullptr);
               }
               nq += __popc(msk);
             }
           }
           __syncwarp();
-          for (int q = lane; q < min(nq, 64); q += 32) rowacc += boundary_point(wq[q]);
+          if (DER) {
+            // the FP64 stencils of up to 6 queued points at once, one ray per lane
+            const int nqq = min(nq, 64);
+            double* bd = &ds.bdist[warp][0][0];
+            for (int q0 = 0; q0 < nqq; q0 += 6) {
+              const int ncq = min(6, nqq - q0);
+              const int pi = lane / 5, k = lane - 5 * pi;
+              if (pi < ncq) {
+                const int l2_ = lo + wq[q0 + pi] + k - 2;
+                bd[pi * 5 + k] = (!B.periodic && (l2_ < 0 || l2_ >= NTH)) ? __longlong_as_double(0x7ff0000000000000LL)
+                                                                          : ray_distance64<NL>(sh, B, i, wrapl(l2_));
+              }
+              __syncwarp();
+              if (lane < ncq) rowacc += boundary_point(wq[q0 + lane], bd + lane * 5);
+              __syncwarp();
+            }
+          } else {
+            for (int q = lane; q < min(nq, 64); q += 32) rowacc += boundary_point(wq[q], nullptr);
+          }
           __syncwarp();
           if (DER) {
             // gradient of every seeded ray's distance, recomputed from its
@@ -1752,13 +1805,10 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += 3 * ((NP + 15) & ~(size_t)15);
   b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
   b += sizeof(int) * NW * 64;  // per-warp boundary queues
-  if (der) {
-    b += sizeof(DerShared);
-    const int seg2 = g.n_theta < 1024 ? g.n_theta : 1024;
-    b += sizeof(float) * NW * (seg2 + 4);
-  }
+  const int segmax = der ? 512 : 1024;
+  const int seg = g.n_theta < segmax ? g.n_theta : segmax;
+  if (der) b += sizeof(DerShared) + sizeof(float) * NW * (seg + 4);  // state and ray seeds
   b += sizeof(cf) * g.n_theta;
-  const int seg = g.n_theta < 1024 ? g.n_theta : 1024;
   b += sizeof(float) * NW * (seg + 4);
   b += sizeof(cdf) * g.n_limb;
   return b;

@@ -99,9 +99,10 @@ def test_dA_adjoint_sets(G, oracle_mod):
 
 
 def test_dA_uniform_and_grid_variants(G, oracle_mod):
+    """Uniform rule; grids with ragged rows, and rows longer than one segment."""
     params, t = I.caustic_crossing_binary(n_epochs=40)
     t = t[:, ::2]
-    for g in (I.grid(uniform=1), I.grid(n_r=37, n_theta=500)):
+    for g in (I.grid(uniform=1), I.grid(n_r=37, n_theta=500), I.grid(n_r=20, n_theta=1100, n_limb=300)):
         A, dA, st, _ = gpu_dA(G, params, t, g)
         Ao, dAo, so = oracle_mod.magnification_fwd(params, t, g)
         assert_dA(dA, dAo, str(g), Ao)
