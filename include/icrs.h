@@ -199,6 +199,108 @@ int icrs_chi2_grad(const icrs_params* p, int S, const double* t, int E,
                    double* chi2, double* grad, double* A, uint32_t* status,
                    void* stream);
 
+/*
+ * ICRS on a list of items of an [S][E] problem: for i < n, item items[i] =
+ * s * E + e runs set s at time t[s][e] and writes A[s][e] (and status[s][e]).
+ * Other entries are left untouched, and an index outside [0, S * E) is
+ * skipped.  This runs the epochs that the surrogate's gate routes back to
+ * ICRS.  Consecutive items of one set reuse the previous item's roots as
+ * starting values, so the listed order matters for speed only.
+ *   items  [n] device int32; the other arguments are as icrs_magnification
+ */
+int icrs_magnification_indexed(const icrs_params* p, int S, const double* t, int E,
+                               const int32_t* items, int n, const icrs_grid* g,
+                               double* A, uint32_t* status, void* stream);
+
+/*
+ * Learned surrogate of the finite-source correction.  It is not in the paper;
+ * the gate below sends uncertain epochs back to ICRS.
+ *   network   7 -> 128 -> 128 -> 128 -> 128 -> 2 with SiLU on the hidden
+ *             layers.  Output 0 is mu, the prediction of y = 1e4 log(A/A_ps);
+ *             output 1 is s, the log-variance of that prediction.
+ *   numerics  BF16 weights, inputs and activations between layers; FP32
+ *             accumulation in tensor memory (tcgen05.mma); FP32 master
+ *             weights and Adam moments.  In the backward pass each layer's
+ *             upstream gradient is rounded to BF16 before its contractions.
+ *   theta     [ICRS_MLP_NPARAM] device float: W0 [128][7], b0 [128],
+ *             W1 [128][128], b1, W2, b2, W3, b3, W4 [2][128], b4 [2],
+ *             each weight row-major [out][in]
+ *   pack      [ICRS_MLP_PACK_BYTES] device bytes (16-byte aligned): the BF16
+ *             weights and their transposes in the tensor-core operand layout,
+ *             written by icrs_mlp_pack or by a training step
+ *   features  [n][8] device float (16-byte aligned): (w_c.x, w_c.y, log10 s,
+ *             (log10 q + 3)/2, log10 rho + 3, 4 (u1 - 0.55),
+ *             clamp(log10 min_j |det J(z_j)|, -6, 1), 0), where z_j are the
+ *             point-source images at the source centre
+ */
+#define ICRS_MLP_NPARAM 50818
+#define ICRS_MLP_PACK_BYTES 208896
+
+/* theta -> pack (BF16 operand tiles). */
+int icrs_mlp_pack(const float* theta, void* pack, void* stream);
+
+/*
+ * Inference: out [n][2] device float = (mu, s) per row of features.  One
+ * persistent tcgen05 kernel.  err: device int32 or NULL, set to 1 if a
+ * tensor-core completion wait ran past its bound (the results are then
+ * invalid).
+ */
+int icrs_mlp_infer(const void* pack, const float* theta, const float* features, int n,
+                   float* out, int* err, void* stream);
+
+/* Bytes of workspace a training step over n samples needs. */
+size_t icrs_mlp_workspace_bytes(int n);
+
+/*
+ * One training step on n samples: the mean Gaussian NLL
+ *     1/2 [(y - mu)^2 e^{-s} + s]
+ * and its gradient, then Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected,
+ * `step` counts from 1) if lr > 0, and the repack of `pack`.
+ *   target     [n] device float: y = 1e4 log(A_ICRS / A_ps)
+ *   grad       [ICRS_MLP_NPARAM] device float or NULL (out): the gradient
+ *   loss       [1] device float or NULL (out)
+ *   workspace  device, 256-byte aligned, >= icrs_mlp_workspace_bytes(n);
+ *              caller-owned (the library allocates nothing)
+ *   adam_m, adam_v  [ICRS_MLP_NPARAM] device float moments (used if lr > 0)
+ * With lr = 0 the step computes the gradient only and leaves theta alone.
+ */
+int icrs_mlp_train_step(float* theta, float* adam_m, float* adam_v, void* pack, int step,
+                        float lr, const float* features, const float* target, int n,
+                        float* grad, float* loss, void* workspace, size_t workspace_bytes,
+                        int* err, void* stream);
+
+/*
+ * Surrogate features of every (set, epoch) of an [S][E] problem (binary lens,
+ * g->n_lens = 2).  The point-source solve at the source centre is the same as
+ * icrs_point_source.
+ *   features  [S][E][8] device float (out)
+ *   A_ps      [S][E] device double (out): point-source magnification
+ *   status    [S][E] device uint32 or NULL (out): the point-source ICRS_ST_* bits
+ */
+int icrs_surrogate_features(const icrs_params* p, int S, const double* t, int E,
+                            const icrs_grid* g, float* features, double* A_ps,
+                            uint32_t* status, void* stream);
+
+/* Bytes of workspace icrs_surrogate_gate needs for n epochs. */
+size_t icrs_surrogate_gate_workspace_bytes(int n);
+
+/*
+ * Error gate.  Epoch i is accepted when all of these hold:
+ *   - its point-source status is 0;
+ *   - features[i][6] >= caustic_min;
+ *   - exp(s_i / 2) <= sigma_max;
+ *   - |mu_i| <= mu_max.
+ * For an accepted epoch, A[i] = A_ps[i] exp(1e-4 mu_i).  Every other epoch is
+ * listed, in increasing order, in routed_idx[0 .. *n_routed) (device outputs)
+ * and its A[i] is left for icrs_magnification_indexed.
+ *   pred [n][2], features [n][8], A_ps [n], st_ps [n]: as produced above
+ *   workspace  device, >= icrs_surrogate_gate_workspace_bytes(n)
+ */
+int icrs_surrogate_gate(const float* pred, const float* features, const double* A_ps,
+                        const uint32_t* st_ps, int n, float sigma_max, float mu_max,
+                        float caustic_min, double* A, int32_t* routed_idx, int32_t* n_routed,
+                        void* workspace, size_t workspace_bytes, void* stream);
+
 /* Message for a return code (static string). */
 const char* icrs_strerror(int code);
 

@@ -1,0 +1,154 @@
+"""FP64 oracle of the learned surrogate (test infrastructure only; the product
+never imports it).
+
+The surrogate is not in the paper.  It is the gated MLP of the build's scope:
+7 features -> 4 x 128 SiLU -> 2 outputs (mu, log-variance s), trained with the
+Gaussian negative log-likelihood 1/2 [(y - mu)^2 e^{-s} + s] and Adam.
+
+Precision convention, mirrored from the CUDA kernels:
+  - weights and inputs are rounded to BF16 (round to nearest even);
+  - every contraction accumulates exactly (here FP64; FP32 on the GPU);
+  - the activations between layers are rounded to BF16;
+  - in the backward pass, the upstream gradient dZ of each layer is rounded
+    to BF16 before it enters its three contractions: dW = dZ^T X,
+    db = sum dZ, dX = dZ W.
+With bf16=False every rounding is skipped, which gives the plain FP64 network
+that the finite-difference pins check.
+
+Parameter vector theta (float32, 50,818 entries), row-major [out][in]:
+  W0 [128][7], b0 [128], W1 [128][128], b1, W2, b2, W3, b3, W4 [2][128], b4 [2].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+NIN, H, NOUT = 7, 128, 2
+SHAPES = [("W0", (H, NIN)), ("b0", (H,)), ("W1", (H, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)),
+          ("W3", (H, H)), ("b3", (H,)), ("W4", (NOUT, H)), ("b4", (NOUT,))]
+N_PARAMS = sum(int(np.prod(s)) for _, s in SHAPES)
+
+
+def bf16_round(x):
+    """Round to the nearest BF16 value, ties to even (via float32: values are
+    first rounded to float32, then the low 16 bits of the float32 pattern are
+    rounded off).  Returns float64."""
+    x32 = np.asarray(x, dtype=np.float64).astype(np.float32)
+    u = x32.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    out = (r & 0xFFFFFFFF).astype(np.uint32).view(np.float32).astype(np.float64)
+    nan = np.isnan(x32)
+    if np.any(nan):
+        out = np.where(nan, np.nan, out)
+    return out
+
+
+def unpack(theta):
+    theta = np.asarray(theta, dtype=np.float64)
+    assert theta.size == N_PARAMS
+    out, o = {}, 0
+    for name, shp in SHAPES:
+        n = int(np.prod(shp))
+        out[name] = theta[o:o + n].reshape(shp)
+        o += n
+    return out
+
+
+def pack(d):
+    return np.concatenate([np.asarray(d[name], dtype=np.float64).ravel() for name, _ in SHAPES])
+
+
+def silu(z):
+    return z / (1.0 + np.exp(-z))
+
+
+def silu_prime(z):
+    sg = 1.0 / (1.0 + np.exp(-z))
+    return sg * (1.0 + z * (1.0 - sg))
+
+
+def init_theta(seed=0):
+    """He-style uniform initialisation; the last layer starts small."""
+    rng = np.random.default_rng(seed)
+    d = {}
+    for name, shp in SHAPES:
+        if name.startswith("b"):
+            d[name] = np.zeros(shp)
+        else:
+            fan_in = shp[1]
+            lim = np.sqrt(6.0 / fan_in) * (0.1 if name == "W4" else 1.0)
+            d[name] = rng.uniform(-lim, lim, shp)
+    return pack(d).astype(np.float32)
+
+
+def forward(theta, X, bf16=True):
+    """X [n, 7] -> Y [n, 2] and the cache for backward."""
+    p = unpack(theta)
+    rnd = bf16_round if bf16 else (lambda v: np.asarray(v, dtype=np.float64))
+    xs = [rnd(X)]
+    zs = []
+    for l in range(4):
+        z = xs[-1] @ rnd(p[f"W{l}"]).T + p[f"b{l}"]
+        zs.append(z)
+        xs.append(rnd(silu(z)))
+    Y = xs[-1] @ rnd(p["W4"]).T + p["b4"]
+    return Y, {"x": xs, "z": zs, "p": p, "bf16": bf16}
+
+
+def nll(Y, y):
+    """Mean Gaussian NLL over the batch and its gradient with respect to Y."""
+    n = Y.shape[0]
+    mu, s = Y[:, 0], Y[:, 1]
+    r = y - mu
+    e = np.exp(-s)
+    L = 0.5 * np.mean(r * r * e + s)
+    dY = np.stack([-r * e, 0.5 * (1.0 - r * r * e)], axis=1) / n
+    return L, dY
+
+
+def backward(cache, dY):
+    """Gradient of the loss with respect to theta (float64 vector)."""
+    p, xs, zs = cache["p"], cache["x"], cache["z"]
+    rnd = bf16_round if cache["bf16"] else (lambda v: np.asarray(v, dtype=np.float64))
+    g = {}
+    dz = rnd(dY)
+    g["W4"] = dz.T @ xs[4]
+    g["b4"] = dz.sum(axis=0)
+    dx = dz @ rnd(p["W4"])
+    for l in range(3, -1, -1):
+        dz = rnd(dx * silu_prime(zs[l]))
+        g[f"W{l}"] = dz.T @ xs[l]
+        g[f"b{l}"] = dz.sum(axis=0)
+        if l > 0:
+            dx = dz @ rnd(p[f"W{l}"])
+    return pack(g)
+
+
+def adam(theta, m, v, grad, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (bias-corrected); step counts from 1.  Returns new
+    (theta, m, v)."""
+    m = b1 * m + (1.0 - b1) * grad
+    v = b2 * v + (1.0 - b2) * grad * grad
+    mh = m / (1.0 - b1 ** step)
+    vh = v / (1.0 - b2 ** step)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def features(p: dict, t, grid: dict):
+    """Surrogate features of one parameter set at times t, from the oracle's
+    point-source images at the source centre: returns (features [n, 8],
+    A_ps [n], status [n]).  det J = 1 - |sum_i eps_i / (z - a_i)^2|^2 (Eq. detJ)."""
+    import oracle
+    w = oracle.source_centre(p, t)
+    A, nimg, z, st = oracle.point_source(p, grid, w)
+    eps, a = oracle.lens(p)
+    out = np.zeros((len(w), 8))
+    for i in range(len(w)):
+        zi = z[i, : nimg[i]]
+        gam = np.sum(eps[None, :] / (zi[:, None] - a[None, :]) ** 2, axis=1)
+        det = np.abs(1.0 - np.abs(gam) ** 2)
+        md = np.min(det) if len(det) else 0.0
+        lg = np.log10(md) if md > 0 else -np.inf
+        out[i] = [w[i].real, w[i].imag, np.log10(p["s"]), (np.log10(p["q"]) + 3.0) / 2.0,
+                  np.log10(p["rho"]) + 3.0, 4.0 * (p["u1"] - 0.55), min(1.0, max(-6.0, lg)), 0.0]
+    return out, A, st

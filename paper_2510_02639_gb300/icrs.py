@@ -21,7 +21,14 @@ ST_NONCONV, ST_IMGCOUNT, ST_SECTCAP, ST_EDGE, ST_NAN, ST_OVERFLOW = 1, 2, 4, 8, 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = ("icrs_grid_default", "icrs_point_source", "icrs_magnification",
             "icrs_magnification_diag", "icrs_magnification_vjp", "icrs_chi2_grad",
+            "icrs_magnification_indexed", "icrs_mlp_pack", "icrs_mlp_infer",
+            "icrs_mlp_workspace_bytes", "icrs_mlp_train_step", "icrs_surrogate_features",
+            "icrs_surrogate_gate_workspace_bytes", "icrs_surrogate_gate",
             "icrs_strerror", "icrs_abi_version")
+
+MLP_NPARAM = 50818
+MLP_PACK_BYTES = 208896
+TARGET_SCALE = 1e4  # the network predicts 1e4 log(A / A_ps)
 
 # Order of the 8 derivative slots of icrs_magnification_vjp / icrs_chi2_grad.
 PARAM_ORDER = ("t0", "tE", "u0", "alpha", "s", "q", "rho", "u1")
@@ -77,6 +84,25 @@ def _load():
     L.icrs_chi2_grad.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid),
                                  vp, vp, vp, vp, vp, vp, vp]
     L.icrs_chi2_grad.restype = ctypes.c_int
+    L.icrs_magnification_indexed.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int,
+                                             ctypes.POINTER(IcrsGrid), vp, vp, vp]
+    L.icrs_magnification_indexed.restype = ctypes.c_int
+    L.icrs_mlp_pack.argtypes = [vp, vp, vp]
+    L.icrs_mlp_pack.restype = ctypes.c_int
+    L.icrs_mlp_infer.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, vp]
+    L.icrs_mlp_infer.restype = ctypes.c_int
+    L.icrs_mlp_workspace_bytes.argtypes = [ctypes.c_int]
+    L.icrs_mlp_workspace_bytes.restype = ctypes.c_size_t
+    L.icrs_mlp_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_float, vp, vp, ctypes.c_int,
+                                      vp, vp, vp, ctypes.c_size_t, vp, vp]
+    L.icrs_mlp_train_step.restype = ctypes.c_int
+    L.icrs_surrogate_features.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid), vp, vp, vp, vp]
+    L.icrs_surrogate_features.restype = ctypes.c_int
+    L.icrs_surrogate_gate_workspace_bytes.argtypes = [ctypes.c_int]
+    L.icrs_surrogate_gate_workspace_bytes.restype = ctypes.c_size_t
+    L.icrs_surrogate_gate.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.icrs_surrogate_gate.restype = ctypes.c_int
     L.icrs_strerror.argtypes = [ctypes.c_int]
     L.icrs_strerror.restype = ctypes.c_char_p
     L.icrs_abi_version.restype = ctypes.c_int
@@ -270,3 +296,85 @@ def magnification_ad(theta, t, grid: IcrsGrid):
     if _MAG_FN is None:
         _MAG_FN = _autograd_function()
     return _MAG_FN.apply(theta, t, grid)
+
+
+def magnification_indexed(params_dev, t, grid: IcrsGrid, items, n, A, status=None, stream=None):
+    """ICRS on items[0:n] (indices s * E + e) of the [S, E] problem; writes
+    A[s, e] (and status) for those items only."""
+    import torch
+    S = params_dev.numel() // PARAMS_DTYPE.itemsize
+    E = t.shape[-1]
+    assert items.dtype == torch.int32 and A.dtype == torch.float64
+    check(lib.icrs_magnification_indexed(_ptr(params_dev), S, _ptr(t), E, _ptr(items), int(n), ctypes.byref(grid),
+                                         _ptr(A), _ptr(status), _stream(torch, stream)))
+    return A
+
+
+def mlp_pack(theta, pack=None, stream=None):
+    import torch
+    if pack is None:
+        pack = torch.empty(MLP_PACK_BYTES, dtype=torch.uint8, device=theta.device)
+    check(lib.icrs_mlp_pack(_ptr(theta), _ptr(pack), _stream(torch, stream)))
+    return pack
+
+
+def mlp_infer(pack, theta, feat, out=None, err=None, stream=None):
+    """feat [n, 8] float32 -> (mu, s) [n, 2] float32."""
+    import torch
+    n = feat.shape[0]
+    assert feat.dtype == torch.float32 and feat.is_contiguous() and feat.shape[1] == 8
+    if out is None:
+        out = torch.empty((n, 2), dtype=torch.float32, device=feat.device)
+    check(lib.icrs_mlp_infer(_ptr(pack), _ptr(theta), _ptr(feat), n, _ptr(out), _ptr(err), _stream(torch, stream)))
+    return out
+
+
+def mlp_workspace(n, device="cuda"):
+    import torch
+    nb = int(lib.icrs_mlp_workspace_bytes(int(n)))
+    return torch.empty(max(nb, 256), dtype=torch.uint8, device=device)
+
+
+def mlp_train_step(theta, m, v, pack, step, lr, feat, target, workspace=None, grad=None, loss=None, err=None,
+                   stream=None):
+    """One training step (Adam if lr > 0).  Returns (grad, loss) tensors
+    (grad/loss may be None when not requested)."""
+    import torch
+    n = feat.shape[0]
+    assert feat.dtype == torch.float32 and target.dtype == torch.float32 and feat.is_contiguous()
+    if workspace is None:
+        workspace = mlp_workspace(n, feat.device)
+    check(lib.icrs_mlp_train_step(_ptr(theta), _ptr(m), _ptr(v), _ptr(pack), int(step), float(lr), _ptr(feat),
+                                  _ptr(target), n, _ptr(grad), _ptr(loss), _ptr(workspace), workspace.numel(),
+                                  _ptr(err), _stream(torch, stream)))
+    return grad, loss
+
+
+def surrogate_features(params_dev, t, grid: IcrsGrid, stream=None):
+    """Returns (features [S*E, 8] f32, A_ps [S*E] f64, status [S*E] int32)."""
+    import torch
+    S = params_dev.numel() // PARAMS_DTYPE.itemsize
+    E = t.shape[-1]
+    feat = torch.empty((S * E, 8), dtype=torch.float32, device=t.device)
+    Aps = torch.empty((S * E,), dtype=torch.float64, device=t.device)
+    st = torch.empty((S * E,), dtype=torch.int32, device=t.device)
+    check(lib.icrs_surrogate_features(_ptr(params_dev), S, _ptr(t), E, ctypes.byref(grid), _ptr(feat), _ptr(Aps),
+                                      _ptr(st), _stream(torch, stream)))
+    return feat, Aps, st
+
+
+def surrogate_gate(pred, feat, A_ps, st_ps, sigma_max, mu_max, caustic_min, A=None, stream=None):
+    """Returns (A [n] f64 with accepted epochs filled, routed_idx [n] int32,
+    n_routed [1] int32 device)."""
+    import torch
+    n = pred.shape[0]
+    dev = pred.device
+    if A is None:
+        A = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    idx = torch.empty((n,), dtype=torch.int32, device=dev)
+    nr = torch.zeros((1,), dtype=torch.int32, device=dev)
+    ws = torch.empty(max(int(lib.icrs_surrogate_gate_workspace_bytes(n)), 256), dtype=torch.uint8, device=dev)
+    check(lib.icrs_surrogate_gate(_ptr(pred), _ptr(feat), _ptr(A_ps), _ptr(st_ps), n, float(sigma_max),
+                                  float(mu_max), float(caustic_min), _ptr(A), _ptr(idx), _ptr(nr), _ptr(ws),
+                                  ws.numel(), _stream(torch, stream)))
+    return A, idx, nr

@@ -1,0 +1,159 @@
+"""GPU parity of the surrogate's kernels against the FP64 oracle
+(oracle/mlp.py): tcgen05 inference, the training step's gradient and Adam
+update, the feature kernel, the gate and the indexed ICRS launch.
+
+Tolerance of the network outputs and gradients.  The oracle mirrors every BF16
+rounding point, and its contractions are exact in FP64.  The GPU accumulates
+in FP32.  So a value that lies within ~1e-7 of a BF16 rounding boundary can
+round the other way.  Such a 1-ulp flip moves that activation by 2^-8 of its
+value and propagates.  The bound for each output is therefore 2^-8 of the
+largest activation-weighted term; the checks use 1e-2 of max |Y| for any
+element and 1e-4 of max |Y| for the median element.  For the gradient:
+relative L2 error <= 1e-2 per layer.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_02639_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_02639_gb300 import build as B
+    B.build()
+    from paper_2510_02639_gb300 import icrs
+    return icrs
+
+
+def rand_features(n, seed):
+    rng = np.random.default_rng(seed)
+    f = np.zeros((n, 8), dtype=np.float32)
+    f[:, 0:2] = rng.uniform(-1.5, 1.5, (n, 2))
+    f[:, 2] = rng.uniform(-0.5, 0.5, n)
+    f[:, 3] = rng.uniform(-1, 1, n)
+    f[:, 4] = rng.uniform(-1, 1, n)
+    f[:, 5] = rng.uniform(-1, 1, n)
+    f[:, 6] = rng.uniform(-6, 1, n)
+    return f
+
+
+def theta_for_test(seed):
+    from oracle import mlp as M
+    th = M.init_theta(seed).astype(np.float64)
+    rng = np.random.default_rng(seed + 100)
+    th += 0.02 * rng.standard_normal(th.size)   # non-zero biases, larger last layer
+    return th.astype(np.float32)
+
+
+def test_infer_matches_oracle(G):
+    import torch
+    from oracle import mlp as M
+    n = 1000  # 8 tiles, the last one ragged
+    f = rand_features(n, 1)
+    th = theta_for_test(2)
+    tt = torch.tensor(th, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    pack = G.mlp_pack(tt)
+    out = G.mlp_infer(pack, tt, torch.tensor(f, device="cuda"), err=err).cpu().numpy()
+    assert int(err.item()) == 0
+    Yo, _ = M.forward(th, f[:, :7].astype(np.float64), bf16=True)
+    d = np.abs(out - Yo)
+    sc = np.abs(Yo).max()
+    print("infer max", d.max() / sc, "median", np.median(d) / sc)
+    assert np.all(np.isfinite(out))
+    assert d.max() <= 1e-2 * sc and np.median(d) <= 1e-4 * sc
+
+
+def test_gradient_and_loss_match_oracle(G):
+    import torch
+    from oracle import mlp as M
+    n = 300  # 3 tiles, ragged
+    f = rand_features(n, 3)
+    y = np.random.default_rng(4).standard_normal(n).astype(np.float32)
+    th = theta_for_test(5)
+    tt = torch.tensor(th, device="cuda")
+    pack = G.mlp_pack(tt)
+    grad = torch.zeros(G.MLP_NPARAM, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    G.mlp_train_step(tt, None, None, pack, 1, 0.0, torch.tensor(f, device="cuda"), torch.tensor(y, device="cuda"),
+                     grad=grad, loss=loss, err=err)
+    assert int(err.item()) == 0
+    Yo, cache = M.forward(th, f[:, :7].astype(np.float64), bf16=True)
+    Lo, dY = M.nll(Yo, y.astype(np.float64))
+    go = M.backward(cache, dY)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - Lo) <= 1e-3 * abs(Lo) + 1e-6
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in M.SHAPES])
+    for i, (name, _) in enumerate(M.SHAPES):
+        a, b = g[offs[i]:offs[i + 1]], go[offs[i]:offs[i + 1]]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        print(name, "grad rel L2", rel)
+        assert rel <= 1e-2, (name, rel)
+
+
+def test_adam_step_matches_oracle(G):
+    import torch
+    from oracle import mlp as M
+    n = 256
+    f = rand_features(n, 6)
+    y = np.random.default_rng(7).standard_normal(n).astype(np.float32)
+    th = theta_for_test(8)
+    tt = torch.tensor(th, device="cuda")
+    m = torch.zeros_like(tt); v = torch.zeros_like(tt)
+    pack = G.mlp_pack(tt)
+    grad = torch.zeros_like(tt)
+    G.mlp_train_step(tt, m, v, pack, 1, 1e-3, torch.tensor(f, device="cuda"), torch.tensor(y, device="cuda"), grad=grad)
+    g = grad.cpu().numpy().astype(np.float64)
+    t2, m2, v2 = M.adam(th.astype(np.float64), np.zeros(th.size), np.zeros(th.size), g, 1, 1e-3)
+    np.testing.assert_allclose(tt.cpu().numpy(), t2, rtol=0, atol=2e-6)
+    np.testing.assert_allclose(m.cpu().numpy(), m2, rtol=1e-6, atol=1e-12)
+    # the repacked BF16 weights follow theta
+    pack2 = G.mlp_pack(tt)
+    assert torch.equal(pack, pack2)
+
+
+def test_features_match_oracle(G, oracle_mod):
+    import torch
+    from oracle import mlp as M
+    params, t = I.binary_batch(n_sets=3, n_epochs=200, seed=31)
+    g = I.grid()
+    pd = G.params_to_device(params)
+    tt = torch.tensor(t, device="cuda")
+    feat, Aps, st = G.surrogate_features(pd, tt, G.grid_from_dict(g, 2))
+    feat = feat.cpu().numpy().reshape(3, 200, 8); Aps = Aps.cpu().numpy().reshape(3, 200)
+    for s in range(3):
+        fo, Ao, so = M.features(params[s], t[s], g)
+        np.testing.assert_allclose(Aps[s], Ao, rtol=1e-9)
+        np.testing.assert_allclose(feat[s][:, :6], fo[:, :6], rtol=1e-6, atol=1e-6)
+        np.testing.assert_allclose(feat[s][:, 6], fo[:, 6], rtol=0, atol=1e-5)
+
+
+def test_gate_and_indexed_icrs(G):
+    import torch
+    params, t = I.binary_batch(n_sets=2, n_epochs=1500, seed=41)
+    g = G.grid_from_dict(I.grid(), 2)
+    pd = G.params_to_device(params)
+    tt = torch.tensor(t, device="cuda")
+    feat, Aps, st = G.surrogate_features(pd, tt, g)
+    n = feat.shape[0]
+    rng = np.random.default_rng(9)
+    pred = torch.tensor(np.stack([rng.uniform(-3, 3, n), rng.uniform(-12, 2, n)], 1).astype(np.float32), device="cuda")
+    A, idx, nr = G.surrogate_gate(pred, feat, Aps, st, sigma_max=0.5, mu_max=2.0, caustic_min=-1.0)
+    k = int(nr.item())
+    p_ = pred.cpu().numpy(); f_ = feat.cpu().numpy(); s_ = st.cpu().numpy(); a_ = Aps.cpu().numpy()
+    ok = (s_ == 0) & (f_[:, 6] >= -1.0) & (np.exp(0.5 * p_[:, 1]) <= 0.5) & (np.abs(p_[:, 0]) <= 2.0)
+    np.testing.assert_array_equal(idx.cpu().numpy()[:k], np.flatnonzero(~ok))
+    Ah = A.cpu().numpy()
+    np.testing.assert_allclose(Ah[ok], a_[ok] * np.exp(p_[ok, 0].astype(np.float64) * 1e-4), rtol=1e-12)
+    # the routed epochs through the indexed launch equal the full launch
+    Afull, _ = G.magnification(pd, tt, g)
+    G.magnification_indexed(pd, tt, g, idx, k, A)
+    Ah = A.cpu().numpy(); Af = Afull.cpu().numpy().ravel()
+    r = np.flatnonzero(~ok)
+    np.testing.assert_allclose(Ah[r], Af[r], rtol=1e-7)

@@ -1,0 +1,86 @@
+"""Pins of the surrogate's FP64 oracle (oracle/mlp.py) against things other
+than itself: finite differences of the loss, torch's BF16 conversion, the
+closed-form first Adam step and the SiLU derivative."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+
+def test_bf16_round_matches_torch():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    x = np.concatenate([rng.standard_normal(5000) * 10.0 ** rng.uniform(-6, 6, 5000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.005859375, 3.0e38, -2.5e-30]])
+    want = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(M.bf16_round(x), want)
+
+
+def test_bf16_ties_to_even():
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 (even: 1); 1 + 3*2^-8
+    # halfway between 1 + 2^-7 and 1 + 2^-6 (even: 1 + 2^-6)
+    assert M.bf16_round(1.0 + 2.0 ** -8) == 1.0
+    assert M.bf16_round(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+
+
+def test_silu_prime_finite_difference():
+    z = np.linspace(-8, 8, 101)
+    h = 1e-6
+    fd = (M.silu(z + h) - M.silu(z - h)) / (2 * h)
+    np.testing.assert_allclose(M.silu_prime(z), fd, rtol=1e-8, atol=1e-10)
+
+
+def test_parameter_count():
+    assert M.N_PARAMS == 7 * 128 + 128 + 3 * (128 * 128 + 128) + 2 * 128 + 2 == 50818
+
+
+def test_backward_matches_finite_differences():
+    """FP64 network without rounding: the analytic gradient of the mean NLL
+    against central differences on randomly chosen parameters of every
+    layer."""
+    rng = np.random.default_rng(2)
+    theta = M.init_theta(3).astype(np.float64)
+    theta += 0.05 * rng.standard_normal(theta.size)
+    X = rng.standard_normal((9, 7))
+    y = rng.standard_normal(9)
+    Y, cache = M.forward(theta, X, bf16=False)
+    L, dY = M.nll(Y, y)
+    g = M.backward(cache, dY)
+    offs = np.cumsum([0] + [int(np.prod(s)) for _, s in M.SHAPES])
+    idx = np.concatenate([rng.integers(offs[i], offs[i + 1], 6) for i in range(len(M.SHAPES))])
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h; tm[i] -= h
+        fd = (M.nll(M.forward(tp, X, bf16=False)[0], y)[0] - M.nll(M.forward(tm, X, bf16=False)[0], y)[0]) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-7 * max(1.0, abs(fd)), (i, g[i], fd)
+
+
+def test_nll_gradient_closed_form():
+    """At s = 0 the NLL is (y - mu)^2 / 2 + const: d/dmu = mu - y, d/ds =
+    (1 - (y - mu)^2) / 2 (per sample, divided by n)."""
+    Y = np.array([[0.3, 0.0], [-1.0, 0.0]])
+    y = np.array([1.0, -0.5])
+    L, dY = M.nll(Y, y)
+    assert abs(L - 0.5 * np.mean((y - Y[:, 0]) ** 2)) < 1e-15
+    np.testing.assert_allclose(dY[:, 0], (Y[:, 0] - y) / 2)
+    np.testing.assert_allclose(dY[:, 1], (1 - (y - Y[:, 0]) ** 2) / 4)
+
+
+def test_adam_first_step_is_signed_lr():
+    """Step 1: m_hat = g, v_hat = g^2, so the update is lr g / (|g| + eps)."""
+    rng = np.random.default_rng(4)
+    th = rng.standard_normal(50)
+    g = rng.standard_normal(50)
+    t2, m, v = M.adam(th, np.zeros(50), np.zeros(50), g, 1, 1e-3)
+    np.testing.assert_allclose(t2, th - 1e-3 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_rounded_forward_is_close_to_exact():
+    """BF16 rounding changes outputs only at the BF16 precision level."""
+    rng = np.random.default_rng(5)
+    theta = M.init_theta(6)
+    X = rng.uniform(-1, 1, (64, 7))
+    Yr, _ = M.forward(theta, X, bf16=True)
+    Ye, _ = M.forward(theta, X, bf16=False)
+    assert np.max(np.abs(Yr - Ye)) < 0.05 * np.max(np.abs(Ye)) + 1e-3
