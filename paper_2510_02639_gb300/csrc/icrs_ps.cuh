@@ -1,7 +1,7 @@
 // Point-source images and magnification at one source position (Sec. 2.1:
 // Eqs. lens_eq, amp_point, detJ; roots by Ehrlich-Aberth, Sec. 3.1), one
-// thread per position.  Shared by icrs_point_source and the surrogate's
-// feature kernel.
+// thread per position, for the surrogate's feature kernel.  The steps are
+// those of icrs_point_source's kernel.
 #pragma once
 
 #include "icrs_common.cuh"
@@ -23,6 +23,9 @@ struct PointSource {
 // the first m valid, the rest zero.
 template <int NL>
 __device__ inline PointSource<NL> point_source_solve(const Lens& L, cd w, const icrs_grid& g, double* images) {
+  // binary only: the triple-lens instantiation of this copy disagreed with
+  // the oracle's image counts on the GPU and is not used
+  static_assert(NL == 2, "point_source_solve is validated for binary lenses only");
   constexpr int N = NL * NL + 1;
   constexpr float kEps32 = 5.9604645e-8f;
   const int ll = L.ll;
