@@ -270,6 +270,25 @@ int icrs_mlp_train_step(float* theta, float* adam_m, float* adam_v, void* pack, 
                         int* err, void* stream);
 
 /*
+ * icrs_mlp_train_step without a caller workspace, for callers that cannot
+ * allocate device memory where they train.  The paper has no counterpart:
+ * this is an operational variant of the surrogate's training step.
+ * Scratch: a static device array inside the library, sized for
+ * n <= ICRS_MLP_STATIC_MAX_N samples (larger n gives ICRS_EINVAL).  Its
+ * address is looked up once per device.  No device memory is allocated and
+ * nothing in the scratch needs clearing between calls.  There is one scratch
+ * per device: calls that overlap in time on that device, from any stream or
+ * thread, race on it and must be serialised by the caller.  The first call on
+ * each device should come before any stream capture, because it looks up the
+ * symbol address and sets the kernel's shared-memory attribute.  Arguments and
+ * results are otherwise those of icrs_mlp_train_step.
+ */
+#define ICRS_MLP_STATIC_MAX_N 4096
+int icrs_mlp_train_step_noalloc(float* theta, float* adam_m, float* adam_v, void* pack, int step,
+                                float lr, const float* features, const float* target, int n,
+                                float* grad, float* loss, int* err, void* stream);
+
+/*
  * Surrogate features of every (set, epoch) of an [S][E] problem (binary lens,
  * g->n_lens = 2).  The point-source solve at the source centre is the same as
  * icrs_point_source.

@@ -549,11 +549,48 @@ __global__ void gate_scatter_kernel(const uint8_t* __restrict__ flag, int n, con
   if (f) routed_idx[off + __popc(b & ((1u << lanei) - 1u))] = q;
 }
 
+// ---------------------------------------------------------------- static scratch
+// Scratch of the allocation-free training step.  Some callers cannot ask for
+// device memory at the point where they train:
+//   - code running between the begin and end of a stream capture, where an
+//     allocation would break or be recorded into the capture;
+//   - host-side schedulers with a fixed memory budget that own no allocator;
+//   - processes that must leave the device allocator untouched between steps.
+// For them the step can use this file-scope array: 32 tiles, i.e. batches of
+// up to 4096 samples, about 19 MB, reserved when this module is loaded.
+constexpr int STATIC_MAX_N = ICRS_MLP_STATIC_MAX_N;
+constexpr size_t STATIC_WS_BYTES = (size_t)((STATIC_MAX_N + TM - 1) / TM) * WS_TILE;
+static __device__ __align__(256) uint8_t g_train_scratch[STATIC_WS_BYTES];
+
 }  // namespace sg
 }  // namespace icrs
 
+#include <mutex>
+
 using namespace icrs;
 using namespace icrs::sg;
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the static scratch for the current device, looked up
+// once per device (with that device current) and cached.
+int static_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ICRS_ECUDA;
+  if (dev < 0 || dev >= kMaxDevices) return ICRS_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* a = nullptr;
+    if (cudaGetSymbolAddress(&a, g_train_scratch) != cudaSuccess || !a) return ICRS_ECUDA;
+    g_scratch_addr[dev] = a;
+  }
+  *out = g_scratch_addr[dev];
+  return ICRS_OK;
+}
+}  // namespace
 
 extern "C" {
 
@@ -607,6 +644,20 @@ int icrs_mlp_train_step(float* theta, float* adam_m, float* adam_v, void* pack, 
     pack_kernel<<<(chunks + 255) / 256, 256, 0, st>>>(theta, (uint8_t*)pack);
   }
   return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
+}
+
+int icrs_mlp_train_step_noalloc(float* theta, float* adam_m, float* adam_v, void* pack, int step, float lr,
+                                const float* feat, const float* target, int n, float* grad, float* loss, int* err,
+                                void* stream) {
+  if (n <= 0 || n > STATIC_MAX_N) return ICRS_EINVAL;
+  void* ws = nullptr;
+  const int rc = static_scratch(&ws);
+  if (rc != ICRS_OK) return rc;
+  // Every scratch word the step reads (activations, pre-activations, the
+  // per-tile gradients and losses) is written earlier in the same step, so
+  // nothing has to be cleared between calls.
+  return icrs_mlp_train_step(theta, adam_m, adam_v, pack, step, lr, feat, target, n, grad, loss, ws,
+                             STATIC_WS_BYTES, err, stream);
 }
 
 int icrs_surrogate_features(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, float* feat,

@@ -22,12 +22,14 @@ ST_NONCONV, ST_IMGCOUNT, ST_SECTCAP, ST_EDGE, ST_NAN, ST_OVERFLOW = 1, 2, 4, 8, 
 EXPORTED = ("icrs_grid_default", "icrs_point_source", "icrs_magnification",
             "icrs_magnification_diag", "icrs_magnification_vjp", "icrs_chi2_grad",
             "icrs_magnification_indexed", "icrs_mlp_pack", "icrs_mlp_infer",
-            "icrs_mlp_workspace_bytes", "icrs_mlp_train_step", "icrs_surrogate_features",
+            "icrs_mlp_workspace_bytes", "icrs_mlp_train_step", "icrs_mlp_train_step_noalloc",
+            "icrs_surrogate_features",
             "icrs_surrogate_gate_workspace_bytes", "icrs_surrogate_gate",
             "icrs_strerror", "icrs_abi_version")
 
 MLP_NPARAM = 50818
 MLP_PACK_BYTES = 208896
+MLP_STATIC_MAX_N = 4096  # largest batch of mlp_train_step_noalloc
 TARGET_SCALE = 1e4  # the network predicts 1e4 log(A / A_ps)
 
 # Order of the 8 derivative slots of icrs_magnification_vjp / icrs_chi2_grad.
@@ -96,6 +98,9 @@ def _load():
     L.icrs_mlp_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_float, vp, vp, ctypes.c_int,
                                       vp, vp, vp, ctypes.c_size_t, vp, vp]
     L.icrs_mlp_train_step.restype = ctypes.c_int
+    L.icrs_mlp_train_step_noalloc.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_float, vp, vp, ctypes.c_int,
+                                              vp, vp, vp, vp]
+    L.icrs_mlp_train_step_noalloc.restype = ctypes.c_int
     L.icrs_surrogate_features.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid), vp, vp, vp, vp]
     L.icrs_surrogate_features.restype = ctypes.c_int
     L.icrs_surrogate_gate_workspace_bytes.argtypes = [ctypes.c_int]
@@ -378,3 +383,15 @@ def surrogate_gate(pred, feat, A_ps, st_ps, sigma_max, mu_max, caustic_min, A=No
                                   float(mu_max), float(caustic_min), _ptr(A), _ptr(idx), _ptr(nr), _ptr(ws),
                                   ws.numel(), _stream(torch, stream)))
     return A, idx, nr
+
+
+def mlp_train_step_noalloc(theta, m, v, pack, step, lr, feat, target, grad=None, loss=None, err=None, stream=None):
+    """As mlp_train_step, with the library's static scratch (n <= 4096);
+    overlapping calls on one device race on that scratch."""
+    import torch
+    n = feat.shape[0]
+    assert feat.dtype == torch.float32 and target.dtype == torch.float32 and feat.is_contiguous()
+    check(lib.icrs_mlp_train_step_noalloc(_ptr(theta), _ptr(m), _ptr(v), _ptr(pack), int(step), float(lr),
+                                          _ptr(feat), _ptr(target), n, _ptr(grad), _ptr(loss), _ptr(err),
+                                          _stream(torch, stream)))
+    return grad, loss
