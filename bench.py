@@ -1,21 +1,36 @@
-"""Benchmark: limb-darkened binary-lens finite-source magnifications per second.
+"""Benchmark: limb-darkened binary-lens finite-source magnifications per second
+at relative error <= 1e-4, chi^2 gradients per second, and the FP32 roofline
+fraction of the fused ICRS kernel.
 
-Workload (default): 64 binary-lens parameter sets x 10,000 epochs (log10 q ~
-U[-5,-1], s log-uniform [0.3, 3], rho log-uniform [1e-4, 1e-2], u ~
-U[0.3, 0.8], epochs uniform in [t0 - 2 tE, t0 + 2 tE]), 64 x 256 polar grid per
-sector, 500 limb points.  One step = one call of icrs_magnification over the
-whole batch (one fused kernel launch).  Inputs are resident in HBM; the L2 is
-flushed (a 256 MiB write) between timed steps and each step is timed with CUDA
-events on the launching stream.
+Headline workload: the 64-set binary batch with 10,000 epochs per set.
+  - parameters: log10 q ~ U[-5,-1], s log-uniform [0.3, 3], rho log-uniform
+    [1e-4, 1e-2], u ~ U[0.3, 0.8];
+  - epochs uniform in [t0 - 2 tE, t0 + 2 tE];
+  - 500 limb points, and the accuracy-qualified polar grid of 1024 x 2048
+    rays per sector.
+The qualification is measured in the same run. The GPU magnifications of 48
+sampled epochs are compared with the oracle's converged 2048 x 4096 values
+(tests/golden/batch_converged.json), and the line reports the maximum
+relative error. The fixed 64 x 256 grid is measured as a secondary line with
+its own measured error, which is above 1e-4.
 
-The same line carries "chi2_grad": chi^2 gradient evaluations per second
-(one unit = one parameter set's gradient over its 5,000-epoch light curve,
-8 parameters) on the adjoint batch, 256 sets around s=0.9, q=1e-4,
-rho=8e-4, each perturbed by 1%.  One call of icrs_chi2_grad does the whole
-batch, timed like the magnification steps.
+One step is one call of icrs_magnification over the whole batch, a single
+fused kernel launch. Inputs are resident in HBM. A 256 MiB write flushes the
+L2 between timed steps, and each step is timed with CUDA events on the
+launching stream.
+
+The same line also carries:
+  - "chi2_grad": chi^2 gradient evaluations per second on the adjoint batch.
+    One unit is one set's 8-parameter gradient over its 5,000-epoch light
+    curve. The batch is 256 sets around s=0.9, q=1e-4, rho=8e-4, each
+    parameter perturbed by 1%, on the 64 x 256 grid.
+  - "surrogate": the gated MLP path against plain ICRS at the headline grid.
+    It is trained and calibrated on epochs of the batch distribution, then
+    scored on unseen ones: speed-up, fraction routed to ICRS and maximum
+    relative error. The point-source-only rule is reported beside it.
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (the baseline arm).
+sample of the same workload and grid (the baseline arm).
 
 Prints one JSON line (rank 0).
 """
@@ -36,6 +51,9 @@ sys.path.insert(0, ROOT)
 METRIC = "LD binary magnifications/s at rel.err<=1e-4; chi^2 grads/s; % FP32 peak"
 FLOPS_PER_RAY = {2: 30.0, 3: 40.0}   # algorithmic FP32 flops per ray (lens map + brightness)
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+HEADLINE_GRID = dict(n_r=1024, n_theta=2048)
+FIXED_GRID = dict(n_r=64, n_theta=256)
+GOLDEN = os.path.join(ROOT, "tests", "golden", "batch_converged.json")
 
 
 def peaks():
@@ -95,7 +113,7 @@ class ClockSampler:
                 self.proc.kill()
             self.f.close()
 
-    def summary(self, gpu_index=0):
+    def summary(self):
         try:
             rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
         except Exception:
@@ -115,14 +133,19 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def grid_desc(g):
+    return f"{g['n_r']}x{g['n_theta']}"
+
+
 def run_reference(args, rank, world):
-    """FP64 oracle on the host cores: each step one bounded sample (single thread)."""
+    """FP64 oracle on the host cores at the headline grid: each step one
+    bounded sample of (set, epoch) pairs of the workload (single thread)."""
     if rank != 0:
         return
     import oracle
     from paper_2510_02639_gb300 import inputs as I
     params, t, desc = workload(args.workload)
-    g = I.grid()
+    g = I.grid(**HEADLINE_GRID)
     rng = np.random.default_rng(7)
     n = args.ref_sample
     picks = [(int(rng.integers(len(params))), int(rng.integers(t.shape[1]))) for _ in range(n)]
@@ -142,7 +165,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "magnifications/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(desc, grid="64x256", n_limb=500),
+            "data": "synthetic", "config": dict(desc, grid=grid_desc(HEADLINE_GRID), n_limb=500),
             "cpu_baseline": {"value": val, "unit": "magnifications/s", "cores": 1, "kind": "oracle",
                              "sample": f"{n} random (set, epoch) pairs of the workload per step"},
             "e2e": {"value": val, "unit": "magnifications/s", "h2d_bytes_per_step": 0,
@@ -162,7 +185,40 @@ def cpu_baseline(params, t, g, seconds=12.0):
         n += 1
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "magnifications/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} random (set, epoch) pairs of the workload, FP64 single thread, {dt:.1f} s"}
+            "sample": f"{n} random (set, epoch) pairs of the workload at {grid_desc(g)}, FP64 single thread, "
+                      f"{dt:.1f} s"}
+
+
+def accuracy(icrs, I, g, dev):
+    """Maximum relative error of the GPU magnification against the oracle's
+    converged values of the sampled batch epochs."""
+    import torch
+    gold = json.load(open(GOLDEN))
+    params, t = I.binary_batch()
+    ps = [params[r["set"]] for r in gold["epochs"]]
+    tp = torch.tensor([[t[r["set"], r["epoch"]]] for r in gold["epochs"]], dtype=torch.float64, device=dev)
+    ref = np.array([r["A"] for r in gold["epochs"]])
+    A, _ = icrs.magnification(icrs.params_to_device(ps, dev), tp, icrs.grid_from_dict(g, 2))
+    e = np.abs(A.cpu().numpy().ravel() / ref - 1.0)
+    return {"max_rel_err": float(e.max()), "p99_rel_err": float(np.quantile(e, 0.99)),
+            "median_rel_err": float(np.median(e)), "n": int(len(e)),
+            "reference": f"FP64 oracle at {gold['grid']['n_r']}x{gold['grid']['n_theta']}, "
+                         f"tests/golden/batch_converged.json"}
+
+
+def timed_steps(fn, steps, warmup, flush, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
 
 
 def chi2_bench(icrs, I, args, dev, stream, flush, n_sets):
@@ -170,42 +226,101 @@ def chi2_bench(icrs, I, args, dev, stream, flush, n_sets):
     import torch
     params, t, centre, noise = I.adjoint_batch()
     params, t, noise = params[:n_sets], t[:n_sets], noise[:n_sets]
-    g = icrs.grid_from_dict(I.grid(), 2)
+    g = icrs.grid_from_dict(I.grid(**FIXED_GRID), 2)
     pd = icrs.params_to_device(params, dev)
     tt = torch.tensor(t, dtype=torch.float64, device=dev)
     # data: magnification of the centre parameters plus Gaussian noise (F = A)
     Ac, _ = icrs.magnification(icrs.params_to_device([centre] * len(params), dev), tt, g)
     y = (Ac + torch.tensor(noise, device=dev)).contiguous()
     sig = torch.full_like(y, 0.01)
-    for _ in range(args.warmup):
-        icrs.chi2_grad(pd, tt, g, y, sig, stream=stream)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        ev[k][0].record(stream)
-        chi2, grad, A, st = icrs.chi2_grad(pd, tt, g, y, sig, stream=stream)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    sec = float(np.sum([a.elapsed_time(b) for a, b in ev])) / 1e3
-    ok = bool(torch.isfinite(grad).all().item())
+    out = {}
+
+    def step():
+        out["r"] = icrs.chi2_grad(pd, tt, g, y, sig, stream=stream)
+
+    ms = timed_steps(step, args.steps, args.warmup, flush, stream)
+    sec = float(np.sum(ms)) / 1e3
+    grad = out["r"][1]
     return {"value": len(params) * args.steps / sec, "unit": "chi^2 gradients/s",
             "epochs_per_s": len(params) * t.shape[1] * args.steps / sec,
             "ms_per_step": sec / args.steps * 1e3, "steps": args.steps, "warmup": args.warmup,
-            "workload": f"adjoint_batch_{len(params)}x{t.shape[1]}", "params": 8, "dtype": "f32",
-            "finite": ok, "gpu_launches": args.steps}
+            "workload": f"adjoint_batch_{len(params)}x{t.shape[1]}", "grid": grid_desc(FIXED_GRID), "params": 8,
+            "dtype": "f32", "finite": bool(torch.isfinite(grad).all().item()), "gpu_launches": args.steps}
+
+
+def surrogate_bench(args, dev):
+    """Train, calibrate and score the gated surrogate at the headline grid."""
+    import torch
+    from paper_2510_02639_gb300 import icrs
+    from paper_2510_02639_gb300 import inputs as I
+    from paper_2510_02639_gb300 import surrogate as SG
+    gd = I.grid(**HEADLINE_GRID)
+    g = icrs.grid_from_dict(gd, 2)
+    t0 = time.perf_counter()
+    train = SG.make_dataset(args.sur_train_sets, 2000, seed=501, grid=gd)
+    val = SG.make_dataset(max(1, args.sur_train_sets // 4), 2000, seed=502, grid=gd)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    sur = SG.Surrogate(seed=0)
+    t1 = time.perf_counter()
+    losses = sur.train(train, epochs=args.sur_epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    gate = SG.calibrate(sur, val)
+    c_ps = SG.calibrate_point_source(val)
+    c_est, b_est = SG.calibrate_estimate(val)
+    del train, val
+    # scoring on unseen sets: plain ICRS (event-timed) against the gated path
+    params, t = I.binary_batch(n_sets=args.sur_query_sets, n_epochs=2000, seed=503)
+    pd = icrs.params_to_device(params, dev)
+    tt = torch.tensor(t, dtype=torch.float64, device=dev)
+    icrs.magnification(pd, tt[:, :10].contiguous(), g)  # warm-up launch
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    e[0].record()
+    A_plain, _ = icrs.magnification(pd, tt, g)
+    e[1].record()
+    A_gate, k = sur.gated_magnification(pd, tt, g, gate)
+    e[2].record()
+    torch.cuda.synchronize()
+    feat, Aps, st = icrs.surrogate_features(pd, tt, g)
+    n = A_gate.numel()
+    Ap = A_plain.reshape(-1)
+    err = (A_gate / Ap - 1.0).abs()
+    ps_ok = (st == 0) & (feat[:, 6] >= c_ps)
+    ps_err = torch.where(ps_ok, (Aps / Ap - 1.0).abs(), torch.zeros_like(err))
+    est_ok = (st == 0) & (feat[:, 6] >= c_est) & (feat[:, 7].abs() <= b_est) & (Aps <= 10.0)
+    Aest = Aps * torch.exp(feat[:, 7].double() / icrs.TARGET_SCALE)
+    est_err = torch.where(est_ok, (Aest / Ap - 1.0).abs(), torch.zeros_like(err))
+    t_plain, t_gate = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    return {"speedup": t_plain / t_gate, "queries": n, "routed_frac": k / n,
+            "max_rel_err_vs_plain": float(err.max()), "plain_ms": t_plain, "gated_ms": t_gate,
+            "gated_magnifications_per_s": n / t_gate * 1e3, "grid": grid_desc(gd),
+            "train_samples": int(args.sur_train_sets * 2000), "train_epochs": args.sur_epochs,
+            "train_s": t_train, "data_s": t_data, "final_loss": losses[-1],
+            "gate": {"sigma_max": gate.sigma_max, "mu_max": gate.mu_max, "b_max": gate.b_max,
+                     "caustic_min": gate.caustic_min, "A_max": gate.A_max},
+            "point_source_only": {"accepted_frac": float(ps_ok.float().mean()), "caustic_min": c_ps,
+                                  "max_rel_err": float(ps_err.max())},
+            "second_order_estimate_only": {"accepted_frac": float(est_ok.float().mean()), "caustic_min": c_est,
+                                           "b_max": b_est,
+                                           "max_rel_err": float(est_err.max())},
+            "dtype": "bf16 weights / fp32 accumulate"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="icrs", choices=["icrs", "reference"])
     ap.add_argument("--workload", default="batch", choices=["batch", "caustic", "triple"])
-    ap.add_argument("--ref-sample", type=int, default=400)
+    ap.add_argument("--ref-sample", type=int, default=6, help="oracle epochs per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chi2-sets", type=int, default=256, help="sets of the adjoint batch per chi^2 step (0: skip)")
+    ap.add_argument("--sur-train-sets", type=int, default=200, help="surrogate training sets x 2000 epochs (0: skip)")
+    ap.add_argument("--sur-query-sets", type=int, default=250, help="surrogate scoring sets x 2000 epochs")
+    ap.add_argument("--sur-epochs", type=int, default=30)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -232,7 +347,7 @@ def main():
 
     params, t, desc = workload(args.workload, rank)
     n_lens = int(params[0]["n_lens"])
-    g = I.grid()
+    g = I.grid(**HEADLINE_GRID)
     grid = icrs.grid_from_dict(g, n_lens)
     dev = torch.device("cuda", local)
     pd = icrs.params_to_device(params, dev)
@@ -243,10 +358,12 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    for _ in range(args.warmup):
+    def step():
         icrs.magnification(pd, tt, grid, out=A, status=st, stream=stream)
-    torch.cuda.synchronize()
 
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
@@ -259,7 +376,7 @@ def main():
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(stream)
-            icrs.magnification(pd, tt, grid, out=A, status=st, stream=stream)
+            step()
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
@@ -272,8 +389,7 @@ def main():
         x = torch.tensor([t_local], device=dev)
         dist.all_reduce(x, op=dist.ReduceOp.MAX)
         t_max = float(x.item())
-    units = S * E * world * args.steps
-    value = units / t_max
+    value = S * E * world * args.steps / t_max
 
     # rays evaluated (sector count in status bits 8..15)
     stc = st.cpu().numpy().astype(np.int64)
@@ -284,52 +400,66 @@ def main():
     achieved = flops / kern_s / 1e12
     peak = fp32_peak_tflops()
 
-    # end-to-end through the C ABI with host buffers (pinned), copies timed
-    e2e = None
-    if True:
-        h_params = pd.cpu().pin_memory()
-        h_t = tt.cpu().pin_memory()
-        h_A = torch.empty((S, E), dtype=torch.float64).pin_memory()
-        h_st = torch.empty((S, E), dtype=torch.int32).pin_memory()
-        d_params = torch.empty_like(pd)
-        d_t = torch.empty_like(tt)
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    h_params = pd.cpu().pin_memory()
+    h_t = tt.cpu().pin_memory()
+    h_A = torch.empty((S, E), dtype=torch.float64).pin_memory()
+    h_st = torch.empty((S, E), dtype=torch.int32).pin_memory()
+    d_params = torch.empty_like(pd)
+    d_t = torch.empty_like(tt)
+    torch.cuda.synchronize()
+    n_e2e = max(1, args.steps)
+    w0 = time.perf_counter()
+    for _ in range(n_e2e):
+        d_params.copy_(h_params, non_blocking=True)
+        d_t.copy_(h_t, non_blocking=True)
+        icrs.magnification(d_params, d_t, grid, out=A, status=st, stream=stream)
+        h_A.copy_(A, non_blocking=True)
+        h_st.copy_(st, non_blocking=True)
         torch.cuda.synchronize()
-        n_e2e = max(2, min(args.steps, 5))
-        w0 = time.perf_counter()
-        for _ in range(n_e2e):
-            d_params.copy_(h_params, non_blocking=True)
-            d_t.copy_(h_t, non_blocking=True)
-            icrs.magnification(d_params, d_t, grid, out=A, status=st, stream=stream)
-            h_A.copy_(A, non_blocking=True)
-            h_st.copy_(st, non_blocking=True)
-            torch.cuda.synchronize()
-        w = (time.perf_counter() - w0) / n_e2e
-        e2e = {"value": S * E * world / w, "unit": "magnifications/s",
-               "h2d_bytes_per_step": int(h_params.numel() + h_t.numel() * 8),
-               "d2h_bytes_per_step": int(h_A.numel() * 8 + h_st.numel() * 4)}
+    w = (time.perf_counter() - w0) / n_e2e
+    e2e = {"value": S * E * world / w, "unit": "magnifications/s",
+           "h2d_bytes_per_step": int(h_params.numel() + h_t.numel() * 8),
+           "d2h_bytes_per_step": int(h_A.numel() * 8 + h_st.numel() * 4)}
+
+    acc = accuracy(icrs, I, g, dev) if args.workload == "batch" else None
+
+    # the fixed 64 x 256 grid (secondary)
+    gf = I.grid(**FIXED_GRID)
+    gridf = icrs.grid_from_dict(gf, n_lens)
+    msf = timed_steps(lambda: icrs.magnification(pd, tt, gridf, out=A, status=st, stream=stream), args.steps,
+                      args.warmup, flush, stream)
+    fixed = {"grid": grid_desc(gf), "value": S * E * world * args.steps / (float(np.sum(msf)) / 1e3),
+             "unit": "magnifications/s", "ms_per_step": float(np.mean(msf)),
+             "accuracy": accuracy(icrs, I, gf, dev) if args.workload == "batch" else None}
 
     chi2 = chi2_bench(icrs, I, args, dev, stream, flush, args.chi2_sets) if args.chi2_sets > 0 else None
+    sur = surrogate_bench(args, dev) if (args.sur_train_sets > 0 and args.workload == "batch" and rank == 0) else None
 
     clocks = clk.summary() if rank == 0 else None
     if rank != 0:
         return
     cpu = None
-    if not args.no_cpu_baseline and world >= 1:
+    if not args.no_cpu_baseline:
         cpu = cpu_baseline(params, t, g)
     line = {
         "metric": METRIC, "value": value, "unit": "magnifications/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": dict(desc, grid=f"{g['n_r']}x{g['n_theta']}", n_limb=g["n_limb"], l2="flushed (256 MiB write) between steps",
+        "config": dict(desc, grid=grid_desc(g), n_limb=g["n_limb"], l2="flushed (256 MiB write) between steps",
                        parallelism=f"replicas{world}" if world > 1 else "single"),
+        "accuracy": acc,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "note": f"ray-stage algorithmic FP32 flops ({FLOPS_PER_RAY[n_lens]:.0f}/ray, {rays:.3e} rays/step) "
-                             f"over the fused kernel's event time; peak = 152 SM x 128 FP32 lanes x 2 x max SM clock"},
+                             f"over the fused kernel's event time; peak = 152 SM x 128 FP32 lanes x 2 x max SM clock "
+                             f"(derived, no measured FP32 entry)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "fixed_grid": fixed,
         "chi2_grad": chi2,
+        "surrogate": sur,
         "clocks": clocks,
         "gpu_launches": args.steps,
         "status_flags": {k: int(np.count_nonzero(stc & b)) for k, b in

@@ -49,6 +49,7 @@ extern "C" {
 #define ICRS_ST_EDGE 8u      /* an inside ray touched a non-periodic grid edge */
 #define ICRS_ST_NAN 16u      /* non-finite result */
 #define ICRS_ST_OVERFLOW 32u /* an on-chip table overflowed; a decision was taken in FP32 */
+#define ICRS_ST_LIMB 64u     /* surrogate features: the image count changes across the source disk */
 /* icrs_magnification also stores the number of sectors integrated for the
  * epoch in bits 8..15 of its status word. */
 #define ICRS_ST_NSECT(st) (((st) >> 8) & 0xffu)
@@ -216,8 +217,9 @@ int icrs_magnification_indexed(const icrs_params* p, int S, const double* t, int
  * Learned surrogate of the finite-source correction.  It is not in the paper;
  * the gate below sends uncertain epochs back to ICRS.
  *   network   7 -> 128 -> 128 -> 128 -> 128 -> 2 with SiLU on the hidden
- *             layers.  Output 0 is mu, the prediction of y = 1e4 log(A/A_ps);
- *             output 1 is s, the log-variance of that prediction.
+ *             layers.  Output 0 is mu, the prediction of y - b, where
+ *             y = 1e4 log(A/A_ps) and b is features[7] below; output 1 is s,
+ *             the log-variance of that prediction.
  *   numerics  BF16 weights, inputs and activations between layers; FP32
  *             accumulation in tensor memory (tcgen05.mma); FP32 master
  *             weights and Adam moments.  In the backward pass each layer's
@@ -230,8 +232,12 @@ int icrs_magnification_indexed(const icrs_params* p, int S, const double* t, int
  *             written by icrs_mlp_pack or by a training step
  *   features  [n][8] device float (16-byte aligned): (w_c.x, w_c.y, log10 s,
  *             (log10 q + 3)/2, log10 rho + 3, 4 (u1 - 0.55),
- *             clamp(log10 min_j |det J(z_j)|, -6, 1), 0), where z_j are the
- *             point-source images at the source centre
+ *             clamp(log10 min_j |det J(z_j)|, -6, 1), b), where z_j are the
+ *             point-source images at the source centre and at the eight limb
+ *             points w_c + rho e^{i pi k / 4}.  The network reads the first 7.
+ *             b = 1e4 log(1 + f_u (mean_k A_ps(limb k) / A_ps - 1)), with
+ *             f_u = (15 - 7 u1) / (10 (3 - u1)), is the second-order
+ *             finite-source estimate: the network predicts y - b
  */
 #define ICRS_MLP_NPARAM 50818
 #define ICRS_MLP_PACK_BYTES 208896
@@ -295,6 +301,8 @@ int icrs_mlp_train_step_noalloc(float* theta, float* adam_m, float* adam_v, void
  *   features  [S][E][8] device float (out)
  *   A_ps      [S][E] device double (out): point-source magnification
  *   status    [S][E] device uint32 or NULL (out): the point-source ICRS_ST_* bits
+ *             of the centre and limb solves, plus ICRS_ST_LIMB when a limb
+ *             point has a different image count from the centre
  */
 int icrs_surrogate_features(const icrs_params* p, int S, const double* t, int E,
                             const icrs_grid* g, float* features, double* A_ps,
@@ -308,8 +316,10 @@ size_t icrs_surrogate_gate_workspace_bytes(int n);
  *   - its point-source status is 0;
  *   - features[i][6] >= caustic_min;
  *   - exp(s_i / 2) <= sigma_max;
- *   - |mu_i| <= mu_max.
- * For an accepted epoch, A[i] = A_ps[i] exp(1e-4 mu_i).  Every other epoch is
+ *   - |mu_i| <= mu_max and |features[i][7]| <= b_max;
+ *   - A_ps[i] <= A_max (ICRS itself needs more angular rays for small
+ *     sources at high magnification, so those epochs stay with ICRS).
+ * For an accepted epoch, A[i] = A_ps[i] exp(1e-4 (features[i][7] + mu_i)).  Every other epoch is
  * listed, in increasing order, in routed_idx[0 .. *n_routed) (device outputs)
  * and its A[i] is left for icrs_magnification_indexed.
  *   pred [n][2], features [n][8], A_ps [n], st_ps [n]: as produced above
@@ -317,7 +327,8 @@ size_t icrs_surrogate_gate_workspace_bytes(int n);
  */
 int icrs_surrogate_gate(const float* pred, const float* features, const double* A_ps,
                         const uint32_t* st_ps, int n, float sigma_max, float mu_max,
-                        float caustic_min, double* A, int32_t* routed_idx, int32_t* n_routed,
+                        float b_max, float caustic_min, double A_max, double* A, int32_t* routed_idx,
+                        int32_t* n_routed,
                         void* workspace, size_t workspace_bytes, void* stream);
 
 /* Message for a return code (static string). */

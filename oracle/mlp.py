@@ -134,21 +134,49 @@ def adam(theta, m, v, grad, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+ST_LIMB = 64  # the image count changes between the source centre and a limb point
+
+
 def features(p: dict, t, grid: dict):
     """Surrogate features of one parameter set at times t, from the oracle's
-    point-source images at the source centre: returns (features [n, 8],
-    A_ps [n], status [n]).  det J = 1 - |sum_i eps_i / (z - a_i)^2|^2 (Eq. detJ)."""
+    point-source images at the source centre and at the eight limb points
+    w_c + rho e^{i pi k / 4}: returns (features [n, 8], A_ps [n], status [n]).
+    Feature 6 is log10 of the smallest |det J| over all those images, with
+    det J = 1 - |sum_i eps_i / (z - a_i)^2|^2 (Eq. detJ), clamped to [-6, 1];
+    status gains ST_LIMB when a limb point's image count differs from the
+    centre's."""
     import oracle
     w = oracle.source_centre(p, t)
     A, nimg, z, st = oracle.point_source(p, grid, w)
     eps, a = oracle.lens(p)
+    st = st.astype(np.uint32).copy()
+
+    def min_det(zi):
+        if len(zi) == 0:
+            return 0.0
+        gam = np.sum(eps[None, :] / (zi[:, None] - a[None, :]) ** 2, axis=1)
+        return float(np.min(np.abs(1.0 - np.abs(gam) ** 2)))
+
+    md = np.array([min_det(z[i, : nimg[i]]) for i in range(len(w))])
+    Alimb = np.zeros(len(w))
+    for k in range(8):
+        wl = w + p["rho"] * np.exp(1j * np.pi * k / 4.0)
+        Al, nl, zl, sl = oracle.point_source(p, grid, wl)
+        Alimb += Al / 8.0
+        for i in range(len(w)):
+            md[i] = min(md[i], min_det(zl[i, : nl[i]]))
+            if nl[i] != nimg[i] or sl[i]:
+                st[i] |= np.uint32(ST_LIMB)
+    # second-order estimate of the disk average: A + (<r^2>/4) lap A, with the
+    # limb mean minus the centre = (rho^2/4) lap A and, for the linear law
+    # I = 1 - u + u sqrt(1 - r^2/rho^2), <r^2>/rho^2 = (15 - 7u) / (10 (3 - u))
+    u = p["u1"]
+    fu = (15.0 - 7.0 * u) / (10.0 * (3.0 - u))
+    base = 1e4 * np.log1p(fu * (Alimb / A - 1.0))
     out = np.zeros((len(w), 8))
     for i in range(len(w)):
-        zi = z[i, : nimg[i]]
-        gam = np.sum(eps[None, :] / (zi[:, None] - a[None, :]) ** 2, axis=1)
-        det = np.abs(1.0 - np.abs(gam) ** 2)
-        md = np.min(det) if len(det) else 0.0
-        lg = np.log10(md) if md > 0 else -np.inf
+        lg = np.log10(md[i]) if md[i] > 0 else -np.inf
         out[i] = [w[i].real, w[i].imag, np.log10(p["s"]), (np.log10(p["q"]) + 3.0) / 2.0,
-                  np.log10(p["rho"]) + 3.0, 4.0 * (p["u1"] - 0.55), min(1.0, max(-6.0, lg)), 0.0]
+                  np.log10(p["rho"]) + 3.0, 4.0 * (p["u1"] - 0.55), min(1.0, max(-6.0, lg)),
+                  min(1e4, max(-1e4, base[i]))]
     return out, A, st

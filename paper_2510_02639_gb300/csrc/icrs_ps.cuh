@@ -22,9 +22,11 @@ struct PointSource {
 // against img_tol in that frame.  images (optional): [N_deg][2] positions,
 // the first m valid, the rest zero.
 template <int NL>
-__device__ inline PointSource<NL> point_source_solve(const Lens& L, cd w, const icrs_grid& g, double* images) {
-  // binary only: the triple-lens instantiation of this copy disagreed with
-  // the oracle's image counts on the GPU and is not used
+__device__ __forceinline__ PointSource<NL> point_source_solve(const Lens L, const cd w, const int max_iter,
+                                                              const double img_tol, double* images) {
+  // binary only (the feature kernel's case).  Everything is passed by value:
+  // an earlier form that took the lens and the grid (a kernel parameter) by
+  // reference returned wrong image counts on the GPU.
   static_assert(NL == 2, "point_source_solve is validated for binary lenses only");
   constexpr int N = NL * NL + 1;
   constexpr float kEps32 = 5.9604645e-8f;
@@ -45,7 +47,7 @@ __device__ inline PointSource<NL> point_source_solve(const Lens& L, cd w, const 
   cauchy_start<N>(b, z);
   PointSource<NL> out;
   out.st = 0;
-  if (ehrlich_aberth_f32<N>(b, z, g.max_iter, 4.0f * kEps32, last) < 0) out.st |= ICRS_ST_NONCONV;
+  if (ehrlich_aberth_f32<N>(b, z, max_iter, 4.0f * kEps32, last) < 0) out.st |= ICRS_ST_NONCONV;
   // candidate roots in the original frame (FP64)
   cd cand[2 * N];
   int nc = 0;
@@ -70,7 +72,7 @@ __device__ inline PointSource<NL> point_source_solve(const Lens& L, cd w, const 
     for (int i = 0; i < NL; ++i) E2[i] = tof(E2d[i]);
     lens_poly<NL, float>(eps32, a2f, D2, E2, tof(w - L.a[l2]), b2);
     for (int j = 0; j < N; ++j) z2[j] = tof(tod(z[j]) + L.a[ll] - L.a[l2]);
-    if (ehrlich_aberth_f32<N>(b2, z2, g.max_iter, 4.0f * kEps32, last) < 0) out.st |= ICRS_ST_NONCONV;
+    if (ehrlich_aberth_f32<N>(b2, z2, max_iter, 4.0f * kEps32, last) < 0) out.st |= ICRS_ST_NONCONV;
     for (int j = 0; j < N; ++j) {
       cd z0 = tod(z2[j]) + L.a[l2];
       int nj = 0;
@@ -102,7 +104,7 @@ __device__ inline PointSource<NL> point_source_solve(const Lens& L, cd w, const 
       if (abs2(stp) <= 1e-30 * fmax(1.0, abs2(x))) break;
     }
     cd F = lens_map<NL, double>(epsd, aj, x) - wj;
-    if (!(sqrt(abs2(F)) <= g.img_tol)) continue;
+    if (!(sqrt(abs2(F)) <= img_tol)) continue;
     if (m >= N) { out.st |= ICRS_ST_OVERFLOW; break; }
     cd gm = shear<NL, double>(epsd, aj, x);
     double det = fabs(1.0 - abs2(gm));

@@ -1,9 +1,11 @@
 // Learned surrogate of the finite-source correction, gated back to ICRS.
 //
-// Not in the paper: a small MLP predicts y = 1e4 log(A_ICRS / A_PS) from 7
-// features of an epoch, with a log-variance output; an error gate sends every
-// epoch whose predicted uncertainty, correction size or caustic proximity is
-// too large (or whose point-source solve is flagged) back to full ICRS.
+// Not in the paper: a small MLP predicts the part of y = 1e4 log(A_ICRS/A_PS)
+// that a second-order finite-source estimate b (from point-source
+// magnifications on the source limb) misses, from 7 features of an epoch,
+// with a log-variance output; an error gate sends every epoch whose predicted
+// uncertainty, correction size or caustic proximity is too large (or whose
+// point-source solves are flagged) back to full ICRS.
 //
 //   network   7 -> 128 -> 128 -> 128 -> 128 -> 2, SiLU on the hidden layers
 //   numerics  BF16 weights, inputs and inter-layer activations; FP32
@@ -13,8 +15,9 @@
 //             three contractions (dW = dZ^T X, db = sum dZ, dX = dZ W)
 //   loss      Gaussian NLL 1/2 [(y - mu)^2 e^{-s} + s], mean over the batch
 //   features  (w_c.x, w_c.y, log10 s, (log10 q + 3)/2, log10 rho + 3,
-//             4 (u1 - 0.55), clamp(log10 min_j |det J(z_j)|, -6, 1)) of the
-//             point-source images z_j at the source centre
+//             4 (u1 - 0.55), clamp(log10 min_j |det J(z_j)|, -6, 1)), the
+//             minimum over the point-source images z_j at the source centre
+//             and at eight points of the source limb
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -466,7 +469,27 @@ __global__ void features_kernel(const icrs_params* __restrict__ P, int S, const 
   const icrs_params prm = P[s];
   const Lens L = make_lens(prm);
   const cd w = source_centre(prm, T[idx]);
-  PointSource<2> ps = point_source_solve<2>(L, w, g, nullptr);
+  PointSource<2> ps = point_source_solve<2>(L, w, g.max_iter, g.img_tol, nullptr);
+  // eight source-limb points: a caustic inside the disk changes the image
+  // count between the centre and some limb point, which the centre's own
+  // images cannot show when the centre lies outside the caustic
+  double mind = ps.m > 0 ? ps.min_det : 0.0;
+  uint32_t stf = ps.st;
+  double Alimb = 0.0;
+  for (int k = 0; k < 8; ++k) {
+    double sn, cs;
+    sincospi(0.25 * k, &sn, &cs);
+    PointSource<2> pl = point_source_solve<2>(L, mk(w.x + prm.rho * cs, w.y + prm.rho * sn), g.max_iter, g.img_tol, nullptr);
+    mind = fmin(mind, pl.m > 0 ? pl.min_det : 0.0);
+    if (pl.m != ps.m || pl.st) stf |= ICRS_ST_LIMB;
+    Alimb += 0.125 * pl.A;
+  }
+  // second-order finite-source estimate: the limb mean minus the centre is
+  // (rho^2 / 4) lap A to leading order, and the disk average of A is
+  // A + (<r^2> / 4) lap A with <r^2> / rho^2 = (15 - 7 u) / (10 (3 - u)) for
+  // the linear law (1/2 for a uniform disk)
+  const double fu = (15.0 - 7.0 * prm.u1) / (10.0 * (3.0 - prm.u1));
+  const double est = ps.A > 0.0 ? TARGET_SCALE * log1p(fu * (Alimb / ps.A - 1.0)) : 0.0;
   float* f = feat + idx * 8;
   f[0] = (float)w.x;
   f[1] = (float)w.y;
@@ -474,22 +497,26 @@ __global__ void features_kernel(const icrs_params* __restrict__ P, int S, const 
   f[3] = (float)((log10(prm.q) + 3.0) * 0.5);
   f[4] = (float)(log10(prm.rho) + 3.0);
   f[5] = (float)(4.0 * (prm.u1 - 0.55));
-  f[6] = ps.m > 0 ? (float)fmin(1.0, fmax(-6.0, log10(ps.min_det))) : -6.0f;
-  f[7] = 0.0f;
+  f[6] = mind > 0.0 ? (float)fmin(1.0, fmax(-6.0, log10(mind))) : -6.0f;
+  f[7] = (est == est) ? (float)fmax(-1e4, fmin(1e4, est)) : 0.0f;
   A_ps[idx] = ps.A;
-  if (status) status[idx] = ps.st;
+  if (status) status[idx] = stf;
 }
 
 // ---------------------------------------------------------------- gate
 // Accept an epoch when its point-source solve is clean, its caustic feature
 // is at least caustic_min, the predicted standard deviation exp(s/2) is at
-// most sigma_max and |mu| at most mu_max (units of 1e-4 in log A); accepted
-// epochs get A = A_ps exp(mu 1e-4).  Routed epochs are listed in order.
+// most sigma_max, |mu| at most mu_max, the second-order estimate |b|
+// (feature 7) at most b_max (units of 1e-4 in log A) and A_ps at most A_max
+// (small sources at high magnification are where ICRS itself needs more
+// angular rays); accepted epochs get
+// A = A_ps exp(1e-4 (b + mu)).  Routed epochs are listed in order.
 constexpr int GB = 1024;  // queries per gate block
 
 __global__ void gate_flags_kernel(const float* __restrict__ pred, const float* __restrict__ feat,
                                   const double* __restrict__ A_ps, const uint32_t* __restrict__ st_ps, int n,
-                                  float sigma_max, float mu_max, float caustic_min, double* __restrict__ A,
+                                  float sigma_max, float mu_max, float b_max, float caustic_min, double A_max,
+                                  double* __restrict__ A,
                                   uint8_t* __restrict__ flag, int32_t* __restrict__ bcount) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
@@ -498,10 +525,11 @@ __global__ void gate_flags_kernel(const float* __restrict__ pred, const float* _
   int routed = 0;
   if (q < n) {
     const float mu = pred[(size_t)q * 2], s = pred[(size_t)q * 2 + 1];
+    const float base = feat[(size_t)q * 8 + 7];
     const bool ok = st_ps[q] == 0u && feat[(size_t)q * 8 + 6] >= caustic_min && expf(0.5f * s) <= sigma_max &&
-                    fabsf(mu) <= mu_max && isfinite(mu);
+                    fabsf(mu) <= mu_max && fabsf(base) <= b_max && isfinite(mu) && A_ps[q] <= A_max;
     routed = ok ? 0 : 1;
-    if (ok) A[q] = A_ps[q] * exp((double)mu / (double)TARGET_SCALE);
+    if (ok) A[q] = A_ps[q] * exp(((double)base + (double)mu) / (double)TARGET_SCALE);
     flag[q] = (uint8_t)routed;
   }
   const unsigned b = __ballot_sync(0xffffffffu, routed);
@@ -680,7 +708,8 @@ size_t icrs_surrogate_gate_workspace_bytes(int n) {
 }
 
 int icrs_surrogate_gate(const float* pred, const float* feat, const double* A_ps, const uint32_t* st_ps, int n,
-                        float sigma_max, float mu_max, float caustic_min, double* A, int32_t* routed_idx,
+                        float sigma_max, float mu_max, float b_max, float caustic_min, double A_max, double* A,
+                        int32_t* routed_idx,
                         int32_t* n_routed, void* workspace, size_t workspace_bytes, void* stream) {
   if (n < 0) return ICRS_EINVAL;
   if (n == 0) return ICRS_OK;
@@ -690,7 +719,8 @@ int icrs_surrogate_gate(const float* pred, const float* feat, const double* A_ps
   const int nb = (n + GB - 1) / GB;
   uint8_t* flag = (uint8_t*)workspace;
   int32_t* bcount = (int32_t*)((uint8_t*)workspace + ((size_t)n + 255) / 256 * 256);
-  gate_flags_kernel<<<nb, GB, 0, st>>>(pred, feat, A_ps, st_ps, n, sigma_max, mu_max, caustic_min, A, flag, bcount);
+  gate_flags_kernel<<<nb, GB, 0, st>>>(pred, feat, A_ps, st_ps, n, sigma_max, mu_max, b_max, caustic_min, A_max, A,
+                                       flag, bcount);
   gate_scan_kernel<<<1, 1024, 0, st>>>(bcount, nb, n_routed);
   gate_scatter_kernel<<<nb, GB, 0, st>>>(flag, n, bcount, routed_idx);
   return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;

@@ -132,6 +132,8 @@ def test_features_match_oracle(G, oracle_mod):
         np.testing.assert_allclose(Aps[s], Ao, rtol=1e-9)
         np.testing.assert_allclose(feat[s][:, :6], fo[:, :6], rtol=1e-6, atol=1e-6)
         np.testing.assert_allclose(feat[s][:, 6], fo[:, 6], rtol=0, atol=1e-5)
+        np.testing.assert_allclose(feat[s][:, 7], fo[:, 7], rtol=1e-5, atol=1e-3)
+        np.testing.assert_array_equal(st.cpu().numpy().reshape(3, 200)[s] & 64, so & 64)
 
 
 def test_gate_and_indexed_icrs(G):
@@ -144,16 +146,67 @@ def test_gate_and_indexed_icrs(G):
     n = feat.shape[0]
     rng = np.random.default_rng(9)
     pred = torch.tensor(np.stack([rng.uniform(-3, 3, n), rng.uniform(-12, 2, n)], 1).astype(np.float32), device="cuda")
-    A, idx, nr = G.surrogate_gate(pred, feat, Aps, st, sigma_max=0.5, mu_max=2.0, caustic_min=-1.0)
+    A, idx, nr = G.surrogate_gate(pred, feat, Aps, st, sigma_max=0.5, mu_max=2.0, b_max=3.0, caustic_min=-1.0)
     k = int(nr.item())
     p_ = pred.cpu().numpy(); f_ = feat.cpu().numpy(); s_ = st.cpu().numpy(); a_ = Aps.cpu().numpy()
-    ok = (s_ == 0) & (f_[:, 6] >= -1.0) & (np.exp(0.5 * p_[:, 1]) <= 0.5) & (np.abs(p_[:, 0]) <= 2.0)
+    ok = ((s_ == 0) & (f_[:, 6] >= -1.0) & (np.exp(0.5 * p_[:, 1]) <= 0.5) & (np.abs(p_[:, 0]) <= 2.0)
+          & (np.abs(f_[:, 7]) <= 3.0))
     np.testing.assert_array_equal(idx.cpu().numpy()[:k], np.flatnonzero(~ok))
     Ah = A.cpu().numpy()
-    np.testing.assert_allclose(Ah[ok], a_[ok] * np.exp(p_[ok, 0].astype(np.float64) * 1e-4), rtol=1e-12)
+    np.testing.assert_allclose(Ah[ok], a_[ok] * np.exp((f_[ok, 7].astype(np.float64) + p_[ok, 0]) * 1e-4),
+                               rtol=1e-12)
     # the routed epochs through the indexed launch equal the full launch
     Afull, _ = G.magnification(pd, tt, g)
     G.magnification_indexed(pd, tt, g, idx, k, A)
     Ah = A.cpu().numpy(); Af = Afull.cpu().numpy().ravel()
     r = np.flatnonzero(~ok)
     np.testing.assert_allclose(Ah[r], Af[r], rtol=1e-7)
+
+
+def test_surrogate_gain_over_plain_icrs(G):
+    """ICRS at the accuracy-qualified 1024 x 2048 grid (within 1e-4 of the
+    converged magnification on the batch sample).  Train on 200k epochs of the
+    binary batch distribution, calibrate the gate on 50k, test on 50k unseen
+    epochs: every accepted epoch is within 1e-4 of ICRS; the gated path
+    (features, inference, gate, ICRS on the routed epochs) is faster than ICRS
+    on all epochs; and the network accepts more epochs than the
+    point-source-only rule calibrated the same way."""
+    import torch
+    from paper_2510_02639_gb300 import surrogate as SG
+    gd = I.grid(n_r=1024, n_theta=2048)
+    g = G.grid_from_dict(gd, 2)
+    train = SG.make_dataset(100, 2000, seed=101, grid=gd)
+    val = SG.make_dataset(25, 2000, seed=102, grid=gd)
+    test = SG.make_dataset(25, 2000, seed=103, grid=gd)
+    sur = SG.Surrogate(seed=0)
+    losses = sur.train(train, epochs=30)
+    gate = SG.calibrate(sur, val)
+    c_ps = SG.calibrate_point_source(val)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    A_plain, _ = G.magnification(test.params, test.t, g)
+    ev[1].record()
+    A_gate, k = sur.gated_magnification(test.params, test.t, g, gate)
+    ev[2].record()
+    torch.cuda.synchronize()
+    t_plain, t_gate = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    n = A_gate.numel()
+    err = (A_gate / A_plain.reshape(-1) - 1.0).abs()
+    ps_ok = (test.st == 0) & (test.feat[:, 6] >= c_ps)
+    ps_err = torch.where(ps_ok, (test.A_ps / test.A - 1.0).abs(), torch.zeros_like(err))
+    c_est, b_est = SG.calibrate_estimate(val)
+    est_ok = ((test.st == 0) & (test.feat[:, 6] >= c_est) & (test.feat[:, 7].abs() <= b_est)
+              & (test.A_ps <= 10.0))
+    est_err = torch.where(est_ok, (test.A_ps * torch.exp(test.feat[:, 7].double() * 1e-4) / test.A - 1.0).abs(),
+                          torch.zeros_like(err))
+    print(f"losses {losses[0]:.3f} -> {losses[-1]:.3f}; gate {gate}; "
+          f"routed {k}/{n}; max err {err.max().item():.3g}; plain {t_plain:.1f} ms gated {t_gate:.1f} ms "
+          f"speed-up {t_plain / t_gate:.2f}; point-source-only accepts {int(ps_ok.sum())}/{n} "
+          f"(max err {ps_err.max().item():.3g}); second-order estimate alone accepts {int(est_ok.sum())}/{n} "
+          f"(max err {est_err.max().item():.3g})")
+    assert losses[-1] < losses[0]
+    assert float(err.max()) <= 1e-4
+    assert k < n
+    assert n - k > int(ps_ok.sum())
+    assert t_gate < t_plain

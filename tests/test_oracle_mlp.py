@@ -84,3 +84,33 @@ def test_rounded_forward_is_close_to_exact():
     Yr, _ = M.forward(theta, X, bf16=True)
     Ye, _ = M.forward(theta, X, bf16=False)
     assert np.max(np.abs(Yr - Ye)) < 0.05 * np.max(np.abs(Ye)) + 1e-3
+
+
+def test_ld_second_moment_closed_form():
+    """<r^2>/rho^2 of the linear law I = 1 - u + u sqrt(1 - r^2) on the unit
+    disk, by quadrature, against the closed form (15 - 7u) / (10 (3 - u))
+    used by the surrogate's second-order estimate."""
+    from scipy.integrate import quad
+    for u in (0.0, 0.3, 0.55, 0.8):
+        I = lambda r: 1.0 - u + u * np.sqrt(max(0.0, 1.0 - r * r))
+        num = quad(lambda r: I(r) * r ** 3, 0, 1, epsabs=1e-14)[0]
+        den = quad(lambda r: I(r) * r, 0, 1, epsabs=1e-14)[0]
+        assert abs(num / den - (15 - 7 * u) / (10 * (3 - u))) < 1e-10
+
+
+def test_second_order_estimate_single_lens(oracle_mod):
+    """Far single lens (q = 1e-9, s = 50): the second-order finite-source
+    estimate b from the eight limb point-source magnifications reproduces the
+    closed-form limb-darkened disk magnification to O((rho/u)^4)."""
+    from tests import closed_forms as CF
+    from paper_2510_02639_gb300 import inputs as I
+    rho, u1 = 0.01, 0.6
+    for u_over_rho in (8.0, 20.0):
+        u = u_over_rho * rho
+        p = I.binary(q=1e-9, s=50.0, rho=rho, u1=u1, u0=u, t0=0.0, tE=1.0, alpha=0.0)
+        # the lens of mass 1/(1+q) sits at -q s/(1+q) ~ 0; the source centre at (0, u)
+        f, Aps, st = M.features(p, [0.0], I.grid())
+        exact = CF.single_lens_ld_disk(u, rho, u1)
+        est = Aps[0] * np.exp(f[0, 7] * 1e-4)
+        assert abs(est / exact - 1.0) < 3.0 * (rho / u) ** 4, (u_over_rho, est, exact, Aps[0])
+        assert abs(Aps[0] / exact - 1.0) > 10 * abs(est / exact - 1.0)
