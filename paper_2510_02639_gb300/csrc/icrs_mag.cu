@@ -1192,7 +1192,9 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       }
       __syncthreads();
       const int gth = sh.gth, gr = sh.gr, mth = sh.mth;
-      const float igth = 1.0f / (float)gth;
+      // group of ray l: l / gth as a multiply-high by ceil(2^32 / gth), exact
+      // for l, gth < 2^16 (here both <= 8192)
+      const unsigned int gmagic = (unsigned int)((0xFFFFFFFFull / (unsigned long long)gth) + 1ull);
       // anchors (FP64, one per thread)
       for (int an = tid; an < sh.nanch; an += NT) {
         int gi = an / mth, mi = an % mth;
@@ -1249,10 +1251,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           // (negative: inside the source; +inf: beyond a non-periodic grid
           // edge); two independent rays per lane and iteration
           auto ray_d2 = [&](int lw, float* d2o) -> bool {
-            int mgrp = __float2int_rz((float)lw * igth);
-            if (mgrp * gth > lw) --mgrp;
-            else if ((mgrp + 1) * gth <= lw) ++mgrp;
-            int o = lw - mgrp * gth;
+            const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
+            const int o = lw - mgrp * gth;
             const Anchor& an_ = anch[gi * mth + mgrp];
             cf t = tab[o];
             cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
@@ -1260,14 +1260,14 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             if constexpr (NL == 2) {
               cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz;
               float n0 = abs2(Q0), n1 = abs2(Q1);
-              float ip = __frcp_rn(n0 * n1);
+              float ip = __fdividef(1.0f, n0 * n1);  // <= 2 ulp, inside the error bound
               cf t0 = an_.K[0] * cj(Q0), t1 = an_.K[1] * cj(Q1);
               U = scl(scl(t0, n1) + scl(t1, n0), ip);
             } else {
               cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz, Q2 = an_.A[2] + dz;
               float n0 = abs2(Q0), n1 = abs2(Q1), n2 = abs2(Q2);
               float n01 = n0 * n1;
-              float ip = __frcp_rn(n01 * n2);
+              float ip = __fdividef(1.0f, n01 * n2);
               cf t0 = an_.K[0] * cj(Q0), t1 = an_.K[1] * cj(Q1), t2 = an_.K[2] * cj(Q2);
               U = scl(scl(t0, n1 * n2) + scl(t1, n0 * n2) + scl(t2, n01), ip);
             }
@@ -1552,9 +1552,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               const float a = ab[m];
               if (a == 0.f) continue;
               const int lw = wrapl(lo + m);
-              int mgrp = __float2int_rz((float)lw * igth);
-              if (mgrp * gth > lw) --mgrp;
-              else if ((mgrp + 1) * gth <= lw) ++mgrp;
+              const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
               const int o = lw - mgrp * gth;
               const Anchor& an_ = anch[gi * mth + mgrp];
               const cf t = tab[o];
