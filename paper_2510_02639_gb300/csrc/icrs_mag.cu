@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(NT, 1)
 mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ T_, int E,
            icrs_grid g, int tiles_per_block, double* __restrict__ A_out, uint32_t* __restrict__ st_out,
            double* __restrict__ diag_sect, int32_t* __restrict__ diag_cnt, float* __restrict__ diag_pts, int PMAX,
-           int has_plo, DerOut dout, const int32_t* __restrict__ items, int n_items) {
+           int has_plo, DerOut dout, const int32_t* __restrict__ items, int n_items, int defer) {
   constexpr int N = NL * NL + 1;
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Shared sh;
@@ -406,7 +406,10 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   const int seg = g.n_theta < segmax ? g.n_theta : segmax;
   float* rowbuf = (float*)p;     p += sizeof(float) * NW * (seg + 4);
   cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
-  int* wqueue = (int*)p;         p += sizeof(int) * NW * 64;  // boundary points of the current row
+  // boundary points of the current row segment; forward binary mode: a
+  // deferred queue of 32 points x 8 words (stencil, row factor, indices)
+  const bool DEFER = !DER && NL == 2 && defer;
+  int* wqueue = (int*)p;         p += sizeof(int) * NW * (DEFER ? 256 : 64);
   // derivative mode: its state and the per-warp ray seeds
   DerShared& ds = *(DerShared*)p;  p += DER ? sizeof(DerShared) : 0;
   DualD* cdual = ds.cx;
@@ -1232,6 +1235,184 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       __syncthreads();
       const float dr32 = sh.dr32;
       const float bxw = (float)(sh.dr64 * sh.dth64);
+      float* dq = (float*)(wqueue + warp * 256);  // deferred boundary points (forward, binary)
+      int dq_n = 0;
+      auto wrapl = [&](int l) -> int { return l < 0 ? l + NTH : (l >= NTH ? l - NTH : l); };
+      // per-point weights (Appendix A).  Points with both neighbours
+      // inside (W = 1) are summed directly; points next to the image
+      // boundary are queued per warp and their crossings solved with one
+      // point per lane.
+      auto brightness = [&](float d2) -> float {
+        if (g.uniform) return I0;
+        float x = fmaxf(0.f, 1.0f - d2 * irho2);
+        float sx = x > 0.f ? x * rsqrtf(x) : 0.f;
+        return I0 * (1.0f - u1f * (1.0f - sx));
+      };
+      // I and dI/dd, dI/drho, dI/du1 at squared distance d2 (linear law:
+      // I = I0 (1 - u1 + u1 sqrt(1 - d^2/rho^2)), I0 = 3 / (pi (3 - u1)))
+      auto brightness_der = [&](float d2, float* Id, float* Ir, float* Iu) -> float {
+        if (g.uniform) { *Id = 0.f; *Ir = 0.f; *Iu = 0.f; return I0; }
+        float x = fmaxf(0.f, 1.0f - d2 * irho2);
+        float sx = x > 0.f ? x * rsqrtf(x) : 0.f;
+        float I = I0 * (1.0f - u1f * (1.0f - sx));
+        float d = sqrtf(d2);
+        float k = sx > 0.f ? I0 * u1f * irho2 / sx : 0.f;
+        *Id = -k * d;
+        *Ir = k * d2 / rho32;
+        *Iu = I / (3.0f - u1f) + I0 * (sx - 1.0f);
+        return I;
+      };
+      // derivative mode: per side, d delta / d(stencil distances) and
+      // d delta / d rho times f'(delta) (crossing p(x) = rho, dx = (drho -
+      // sum_m l_m(x) dy_m) / p'(x); delta = -x on the left, x on the right).
+      // p'(x) is a difference of nearly equal distances, so the stencil
+      // and the crossing are taken in FP64 in this mode.
+      float sd_c[2], sd_l[2][4];
+      int sd_b[2], sd_n[2];
+      // dist (derivative mode): FP64 distances of rays mi-2 .. mi+2 (inf
+      // beyond a non-periodic edge), or NULL to compute them here
+      // sv[k] = signed squared distance of ray l - 2 + k (sv[2] is the
+      // point), lab = l (absolute index), irow = its row
+      auto boundary_weight = [&](int mi, const float* sv, int lab, int irow, const double* dist) -> float {
+        float d2 = -sv[2];
+        float vl = sv[1], vr = sv[3];
+        bool Lin = signbit(vl), Rin = signbit(vr);
+        float W;
+          float fL = 0.f, fR = 0.f;
+          if (DER) { sd_n[0] = sd_n[1] = 0; sd_c[0] = sd_c[1] = 0.f; }
+          for (int side = 0; side < 2; ++side) {
+            bool isL = side == 0;
+            if (isL ? Lin : Rin) continue;
+            float vo = isL ? vl : vr;
+            float delta;
+            if (isinf(vo)) {
+              delta = 0.5f;
+              st_local |= ICRS_ST_EDGE;
+            } else if (DER) {
+              // FP64 stencil; FP32 regula falsi, then Newton on the FP64
+              // cubic; f, f' and the basis in FP32 at the FP64 crossing
+              const int c0 = isL ? -2 : -1;
+              double xsd[4], ysd[4];
+              float ysf[4];
+              int nd = 0;
+              double yin = 0, yout = 0;
+              for (int c = 0; c < 4; ++c) {
+                const int off = c0 + c;
+                double v;
+                if (dist) {
+                  v = dist[off + 2];
+                } else {
+                  const int l2_ = lab + off;
+                  v = (!B.periodic && (l2_ < 0 || l2_ >= NTH)) ? __longlong_as_double(0x7ff0000000000000LL)
+                                                               : ray_distance64<NL>(sh, B, irow, wrapl(l2_));
+                }
+                if (isinf(v)) { st_local |= ICRS_ST_EDGE; continue; }
+                xsd[nd] = (double)off;
+                ysd[nd] = v;
+                ysf[nd] = (float)v;
+                if (off == 0) yin = v;
+                if (off == (isL ? -1 : 1)) yout = v;
+                ++nd;
+              }
+              const double dd1 = ysd[1] - ysd[0];
+              const double dd2 = nd > 2 ? 0.5 * (ysd[2] - 2.0 * ysd[1] + ysd[0]) : 0.0;
+              const double dd3 = nd > 3 ? (ysd[3] - 3.0 * ysd[2] + 3.0 * ysd[1] - ysd[0]) * (1.0 / 6.0) : 0.0;
+              double xd = crossing_solve<float>(ysf, (float)xsd[0], nd, (float)yin, (float)yout, isL ? -1.0f : 1.0f,
+                                                rho32, 1e-5f, 12);
+              bool ok = true;
+              for (int it = 0; it < 2; ++it) {
+                const double tt = xd - xsd[0];
+                const double pv = ysd[0] + tt * (dd1 + (tt - 1.0) * (dd2 + (tt - 2.0) * dd3)) - sh.rho;
+                const double pd = dd1 + (2.0 * tt - 1.0) * dd2 + ((3.0 * tt - 6.0) * tt + 2.0) * dd3;
+                if (!(pd != 0.0)) { ok = false; break; }
+                xd -= pv / pd;
+              }
+              if (!ok || !(isL ? (xd >= -1.0 && xd <= 0.0) : (xd >= 0.0 && xd <= 1.0)))
+                xd = crossing_solve<double>(ysd, xsd[0], nd, yin, yout, isL ? -1.0 : 1.0, sh.rho, 1e-14, 60);
+              const double dd = isL ? -xd : xd;
+              const float dl = (float)dd;
+              float fv, fp;
+              if (g.uniform) { fv = dl + 0.5f; fp = 1.0f; }
+              else if (dd >= g.delta_c) {
+                const float sq = sqrtf(1.0f + 0.5f / dl);
+                fv = (0.5f + dl) * (2.0f / 3.0f) * sq;
+                fp = (2.0f / 3.0f) * sq - (0.5f + dl) / (6.0f * dl * dl * sq);
+              } else { fv = (2.0f / 3.0f) * dl + 0.5f; fp = 2.0f / 3.0f; }
+              if (isL) fL = fv; else fR = fv;
+              const double tt = xd - xsd[0];
+              const double slope = dd1 + (2.0 * tt - 1.0) * dd2 + ((3.0 * tt - 6.0) * tt + 2.0) * dd3;
+              (void)lagrange_basis<float>(ysf, nd, (float)tt, sd_l[side]);
+              sd_c[side] = (float)((isL ? -fp : fp) / slope);
+              sd_b[side] = mi + (int)xsd[0];
+              sd_n[side] = nd;
+              continue;
+            } else {
+              // stencil: entering (-2,-1,0,+1), exiting (-1,0,+1,+2)
+              float xs[4], ys[4];
+              int np_ = 0;
+              const int c0 = isL ? -2 : -1;
+              for (int c = 0; c < 4; ++c) {
+                float vv = sv[2 + c0 + c];
+                if (isinf(vv)) { st_local |= ICRS_ST_EDGE; continue; }
+                xs[np_] = (float)(c0 + c);
+                ys[np_] = sqrtf(fabsf(vv));
+                ++np_;
+              }
+              float xo = isL ? -1.0f : 1.0f;
+              float x = crossing_solve<float>(ys, xs[0], np_, sqrtf(d2), sqrtf(fabsf(vo)), xo, rho32, 1e-5f, 12);
+              delta = isL ? -x : x;
+              if (!g.uniform && fabsf(delta - dcf) < 2e-3f) {
+                // branch of f(delta) too close to call in FP32: redo the
+                // crossing from FP64 distances
+                int l = lab;
+                double xsd[4], ysd[4];
+                int nd = 0;
+                double yin = 0, yout = 0;
+                for (int c = 0; c < 4; ++c) {
+                  int ll2 = l + c0 + c;
+                  if (!B.periodic && (ll2 < 0 || ll2 >= NTH)) continue;
+                  int lw2 = ((ll2 % NTH) + NTH) % NTH;
+                  xsd[nd] = (double)(c0 + c);
+                  ysd[nd] = ray_distance64<NL>(sh, B, irow, lw2);
+                  if (c0 + c == 0) yin = ysd[nd];
+                  if (c0 + c == (isL ? -1 : 1)) yout = ysd[nd];
+                  ++nd;
+                }
+                if (diag_cnt) atomicAdd(&sh.cnt[3], 1);
+                double xd = crossing_solve<double>(ysd, xsd[0], nd, yin, yout, isL ? -1.0 : 1.0, sh.rho, 1e-14, 60);
+                double dd = isL ? -xd : xd;
+                delta = (float)dd;
+                float fv = (float)fdelta<double>(dd, g.delta_c, 0);
+                if (isL) fL = fv; else fR = fv;
+                continue;
+              }
+            }
+            float fv = fdelta<float>(delta, dcf, g.uniform);
+            if (isL) fL = fv; else fR = fv;
+          }
+          if (Lin) W = fR;
+          else if (Rin) W = fL;
+          else W = fmaxf(0.f, fL + fR - 1.0f);
+          if (DER && !(Lin || Rin) && !(fL + fR - 1.0f > 0.f)) sd_n[0] = sd_n[1] = 0, sd_c[0] = sd_c[1] = 0.f;
+        return W;
+      };
+      // deferred boundary points (forward, binary): one per lane, the term
+      // r_i dr dth I W straight into this thread's compensated sum
+      auto flush_deferred = [&]() {
+        __syncwarp();
+        if (lane < dq_n) {
+          const float* e_ = dq + lane * 8;
+          const float I = brightness(-e_[2]);
+          const float W = boundary_weight(0, e_, __float_as_int(e_[6]), __float_as_int(e_[7]), nullptr);
+          const float term = e_[5] * I * W;
+          const float y = term - acc_c;
+          const float tt = acc_s + y;
+          acc_c = (tt - acc_s) - y;
+          acc_s = tt;
+        }
+        __syncwarp();
+        dq_n = 0;
+      };
       for (int i = warp; i < NR; i += NW) {
         const int gi = i / gr;
         const float dri = ((float)(i - gi * gr) + 0.5f - 0.5f * (float)gr) * dr32;
@@ -1278,7 +1459,6 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             *d2o = d2;
             return fabsf(d2 - rho32 * rho32) <= 2.0f * rho32 * eb + eb * eb;  // FP32 cannot decide
           };
-          auto wrapl = [&](int l) -> int { return l < 0 ? l + NTH : (l >= NTH ? l - NTH : l); };
           for (int m0 = lane; m0 < cnt; m0 += 64) {
             const int m1 = m0 + 32;
             const int l0 = lo + m0, l1 = lo + m1;
@@ -1311,168 +1491,12 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           if (DER)
             for (int m = lane; m < cnt; m += 32) ab[m] = 0.f;
           __syncwarp();
-          // per-point weights (Appendix A).  Points with both neighbours
-          // inside (W = 1) are summed directly; points next to the image
-          // boundary are queued per warp and their crossings solved with one
-          // point per lane.
-          auto brightness = [&](float d2) -> float {
-            if (g.uniform) return I0;
-            float x = fmaxf(0.f, 1.0f - d2 * irho2);
-            float sx = x > 0.f ? x * rsqrtf(x) : 0.f;
-            return I0 * (1.0f - u1f * (1.0f - sx));
-          };
-          // I and dI/dd, dI/drho, dI/du1 at squared distance d2 (linear law:
-          // I = I0 (1 - u1 + u1 sqrt(1 - d^2/rho^2)), I0 = 3 / (pi (3 - u1)))
-          auto brightness_der = [&](float d2, float* Id, float* Ir, float* Iu) -> float {
-            if (g.uniform) { *Id = 0.f; *Ir = 0.f; *Iu = 0.f; return I0; }
-            float x = fmaxf(0.f, 1.0f - d2 * irho2);
-            float sx = x > 0.f ? x * rsqrtf(x) : 0.f;
-            float I = I0 * (1.0f - u1f * (1.0f - sx));
-            float d = sqrtf(d2);
-            float k = sx > 0.f ? I0 * u1f * irho2 / sx : 0.f;
-            *Id = -k * d;
-            *Ir = k * d2 / rho32;
-            *Iu = I / (3.0f - u1f) + I0 * (sx - 1.0f);
-            return I;
-          };
-          // derivative mode: per side, d delta / d(stencil distances) and
-          // d delta / d rho times f'(delta) (crossing p(x) = rho, dx = (drho -
-          // sum_m l_m(x) dy_m) / p'(x); delta = -x on the left, x on the right).
-          // p'(x) is a difference of nearly equal distances, so the stencil
-          // and the crossing are taken in FP64 in this mode.
-          float sd_c[2], sd_l[2][4];
-          int sd_b[2], sd_n[2];
-          // dist (derivative mode): FP64 distances of rays mi-2 .. mi+2 (inf
-          // beyond a non-periodic edge), or NULL to compute them here
-          auto boundary_weight = [&](int mi, const double* dist) -> float {
-            float d2 = -buf[mi];
-            float vl = buf[mi - 1], vr = buf[mi + 1];
-            bool Lin = signbit(vl), Rin = signbit(vr);
-            float W;
-              float fL = 0.f, fR = 0.f;
-              if (DER) { sd_n[0] = sd_n[1] = 0; sd_c[0] = sd_c[1] = 0.f; }
-              for (int side = 0; side < 2; ++side) {
-                bool isL = side == 0;
-                if (isL ? Lin : Rin) continue;
-                float vo = isL ? vl : vr;
-                float delta;
-                if (isinf(vo)) {
-                  delta = 0.5f;
-                  st_local |= ICRS_ST_EDGE;
-                } else if (DER) {
-                  // FP64 stencil; FP32 regula falsi, then Newton on the FP64
-                  // cubic; f, f' and the basis in FP32 at the FP64 crossing
-                  const int c0 = isL ? -2 : -1;
-                  double xsd[4], ysd[4];
-                  float ysf[4];
-                  int nd = 0;
-                  double yin = 0, yout = 0;
-                  for (int c = 0; c < 4; ++c) {
-                    const int off = c0 + c;
-                    double v;
-                    if (dist) {
-                      v = dist[off + 2];
-                    } else {
-                      const int l2_ = lo + mi + off;
-                      v = (!B.periodic && (l2_ < 0 || l2_ >= NTH)) ? __longlong_as_double(0x7ff0000000000000LL)
-                                                                   : ray_distance64<NL>(sh, B, i, wrapl(l2_));
-                    }
-                    if (isinf(v)) { st_local |= ICRS_ST_EDGE; continue; }
-                    xsd[nd] = (double)off;
-                    ysd[nd] = v;
-                    ysf[nd] = (float)v;
-                    if (off == 0) yin = v;
-                    if (off == (isL ? -1 : 1)) yout = v;
-                    ++nd;
-                  }
-                  const double dd1 = ysd[1] - ysd[0];
-                  const double dd2 = nd > 2 ? 0.5 * (ysd[2] - 2.0 * ysd[1] + ysd[0]) : 0.0;
-                  const double dd3 = nd > 3 ? (ysd[3] - 3.0 * ysd[2] + 3.0 * ysd[1] - ysd[0]) * (1.0 / 6.0) : 0.0;
-                  double xd = crossing_solve<float>(ysf, (float)xsd[0], nd, (float)yin, (float)yout, isL ? -1.0f : 1.0f,
-                                                    rho32, 1e-5f, 12);
-                  bool ok = true;
-                  for (int it = 0; it < 2; ++it) {
-                    const double tt = xd - xsd[0];
-                    const double pv = ysd[0] + tt * (dd1 + (tt - 1.0) * (dd2 + (tt - 2.0) * dd3)) - sh.rho;
-                    const double pd = dd1 + (2.0 * tt - 1.0) * dd2 + ((3.0 * tt - 6.0) * tt + 2.0) * dd3;
-                    if (!(pd != 0.0)) { ok = false; break; }
-                    xd -= pv / pd;
-                  }
-                  if (!ok || !(isL ? (xd >= -1.0 && xd <= 0.0) : (xd >= 0.0 && xd <= 1.0)))
-                    xd = crossing_solve<double>(ysd, xsd[0], nd, yin, yout, isL ? -1.0 : 1.0, sh.rho, 1e-14, 60);
-                  const double dd = isL ? -xd : xd;
-                  const float dl = (float)dd;
-                  float fv, fp;
-                  if (g.uniform) { fv = dl + 0.5f; fp = 1.0f; }
-                  else if (dd >= g.delta_c) {
-                    const float sq = sqrtf(1.0f + 0.5f / dl);
-                    fv = (0.5f + dl) * (2.0f / 3.0f) * sq;
-                    fp = (2.0f / 3.0f) * sq - (0.5f + dl) / (6.0f * dl * dl * sq);
-                  } else { fv = (2.0f / 3.0f) * dl + 0.5f; fp = 2.0f / 3.0f; }
-                  if (isL) fL = fv; else fR = fv;
-                  const double tt = xd - xsd[0];
-                  const double slope = dd1 + (2.0 * tt - 1.0) * dd2 + ((3.0 * tt - 6.0) * tt + 2.0) * dd3;
-                  (void)lagrange_basis<float>(ysf, nd, (float)tt, sd_l[side]);
-                  sd_c[side] = (float)((isL ? -fp : fp) / slope);
-                  sd_b[side] = mi + (int)xsd[0];
-                  sd_n[side] = nd;
-                  continue;
-                } else {
-                  // stencil: entering (-2,-1,0,+1), exiting (-1,0,+1,+2)
-                  float xs[4], ys[4];
-                  int np_ = 0;
-                  const int c0 = isL ? -2 : -1;
-                  for (int c = 0; c < 4; ++c) {
-                    float vv = buf[mi + c0 + c];
-                    if (isinf(vv)) { st_local |= ICRS_ST_EDGE; continue; }
-                    xs[np_] = (float)(c0 + c);
-                    ys[np_] = sqrtf(fabsf(vv));
-                    ++np_;
-                  }
-                  float xo = isL ? -1.0f : 1.0f;
-                  float x = crossing_solve<float>(ys, xs[0], np_, sqrtf(d2), sqrtf(fabsf(vo)), xo, rho32, 1e-5f, 12);
-                  delta = isL ? -x : x;
-                  if (!g.uniform && fabsf(delta - dcf) < 2e-3f) {
-                    // branch of f(delta) too close to call in FP32: redo the
-                    // crossing from FP64 distances
-                    int l = lo + mi;
-                    double xsd[4], ysd[4];
-                    int nd = 0;
-                    double yin = 0, yout = 0;
-                    for (int c = 0; c < 4; ++c) {
-                      int ll2 = l + c0 + c;
-                      if (!B.periodic && (ll2 < 0 || ll2 >= NTH)) continue;
-                      int lw2 = ((ll2 % NTH) + NTH) % NTH;
-                      xsd[nd] = (double)(c0 + c);
-                      ysd[nd] = ray_distance64<NL>(sh, B, i, lw2);
-                      if (c0 + c == 0) yin = ysd[nd];
-                      if (c0 + c == (isL ? -1 : 1)) yout = ysd[nd];
-                      ++nd;
-                    }
-                    if (diag_cnt) atomicAdd(&sh.cnt[3], 1);
-                    double xd = crossing_solve<double>(ysd, xsd[0], nd, yin, yout, isL ? -1.0 : 1.0, sh.rho, 1e-14, 60);
-                    double dd = isL ? -xd : xd;
-                    delta = (float)dd;
-                    float fv = (float)fdelta<double>(dd, g.delta_c, 0);
-                    if (isL) fL = fv; else fR = fv;
-                    continue;
-                  }
-                }
-                float fv = fdelta<float>(delta, dcf, g.uniform);
-                if (isL) fL = fv; else fR = fv;
-              }
-              if (Lin) W = fR;
-              else if (Rin) W = fL;
-              else W = fmaxf(0.f, fL + fR - 1.0f);
-              if (DER && !(Lin || Rin) && !(fL + fR - 1.0f > 0.f)) sd_n[0] = sd_n[1] = 0, sd_c[0] = sd_c[1] = 0.f;
-            return W;
-          };
           // contribution I W of boundary point mi; derivative mode: its seeds
           auto boundary_point = [&](int mi, const double* dist) -> float {
-            if (!DER) return brightness(-buf[mi]) * boundary_weight(mi, dist);
+            if (!DER) return brightness(-buf[mi]) * boundary_weight(mi, buf + mi - 2, lo + mi, i, dist);
             float Id, Ir, Iu;
             float I = brightness_der(-buf[mi], &Id, &Ir, &Iu);
-            float W = boundary_weight(mi, dist);
+            float W = boundary_weight(mi, buf + mi - 2, lo + mi, i, dist);
             atomicAdd(&ab[mi], W * Id);
             pg[5] += W * Ir;
             pg[6] += W * Iu;
@@ -1510,7 +1534,19 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               }
             }
             unsigned msk = __ballot_sync(0xffffffffu, edge);
-            if (msk) {
+            if (DEFER && msk) {
+              // keep the point's stencil, row factor and indices; solve 32 at
+              // a time (one per lane) when the queue would overflow
+              if (dq_n + __popc(msk) > 32) { flush_deferred(); }
+              if (edge) {
+                float* e_ = dq + (dq_n + __popc(msk & ((1u << lane) - 1u))) * 8;
+                for (int k = 0; k < 5; ++k) e_[k] = buf[mi - 2 + k];
+                e_[5] = ri * bxw;
+                e_[6] = __int_as_float(lo + mi);
+                e_[7] = __int_as_float(i);
+              }
+              dq_n += __popc(msk);
+            } else if (msk) {
               int pos = nq + __popc(msk & ((1u << lane) - 1u));
               if (edge) {
                 if (pos < 64) wq[pos] = mi;
@@ -1619,6 +1655,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         acc_c = (tt - acc_s) - y;
         acc_s = tt;
       }
+      if (DEFER) flush_deferred();
       __syncthreads();
       if (DER && tid < 12) {
         double sum = 0.0;
@@ -1797,7 +1834,7 @@ __global__ void point_source_kernel(const icrs_params* __restrict__ P, int S, co
 }
 
 // ---------------------------------------------------------------- host side
-static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, bool der) {
+static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, bool der, int defer) {
   const int N = NL * NL + 1;
   const size_t NP = (size_t)g.n_limb * N;
   size_t b = has_plo ? sizeof(cf) * NP : 0;
@@ -1805,7 +1842,7 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += sizeof(short) * ((NP + 7) & ~(size_t)7);
   b += 3 * ((NP + 15) & ~(size_t)15);
   b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
-  b += sizeof(int) * NW * 64;  // per-warp boundary queues
+  b += sizeof(int) * NW * ((!der && NL == 2 && defer) ? 256 : 64);  // per-warp boundary queues
   const int segmax = der ? 512 : 1024;
   const int seg = g.n_theta < segmax ? g.n_theta : segmax;
   if (der) b += sizeof(DerShared) + sizeof(float) * NW * (seg + 4);  // state and ray seeds
@@ -1853,13 +1890,19 @@ static int launch_inst(const icrs_params* p, int S, const double* t, int E, cons
   int optin = 0, nsm = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return ICRS_ECUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ICRS_ECUDA;
+  // shared memory: the deferred boundary queue (binary forward) if it fits,
+  // then the lo parts of image positions if they fit, then the FP64 point
+  // table grows to at most 2048 entries
+  auto fits = [&](int pm, int plo, int df) {
+    return mag_smem_bytes(NL, *g, pm, plo, DER, df) + sizeof(Shared) <= (size_t)optin;
+  };
   int pmax = PMAX_MIN;
-  int has_plo = 1;  // keep the lo part of image positions when it fits
-  if (mag_smem_bytes(NL, *g, pmax, has_plo, DER) + sizeof(Shared) > (size_t)optin) has_plo = 0;
-  size_t smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER);
-  if (smem + sizeof(Shared) > (size_t)optin) return ICRS_EUNSUPPORTED;
-  while (pmax < 2048 && mag_smem_bytes(NL, *g, pmax * 2, has_plo, DER) + sizeof(Shared) <= (size_t)optin) pmax *= 2;
-  smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER);
+  int defer = (NL == 2 && !DER) ? 1 : 0;
+  if (!fits(pmax, 0, defer)) defer = 0;
+  int has_plo = fits(pmax, 1, defer) ? 1 : 0;
+  if (!fits(pmax, has_plo, defer)) return ICRS_EUNSUPPORTED;
+  while (pmax < 2048 && fits(pmax * 2, has_plo, defer)) pmax *= 2;
+  size_t smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER, defer);
   if (cudaFuncSetAttribute(mag_kernel<NL, DER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return ICRS_ECUDA;
   int per_sm = 0;
@@ -1871,7 +1914,7 @@ static int launch_inst(const icrs_params* p, int S, const double* t, int E, cons
   if (per_block < 1) per_block = 1;
   long long blocks = (tiles + per_block - 1) / per_block;
   mag_kernel<NL, DER><<<(unsigned)blocks, NT, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect, dcnt,
-                                                          dpts, pmax, has_plo, dout, items, n_items);
+                                                          dpts, pmax, has_plo, dout, items, n_items, defer);
   return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
 }
 
