@@ -1459,33 +1459,35 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             *d2o = d2;
             return fabsf(d2 - rho32 * rho32) <= 2.0f * rho32 * eb + eb * eb;  // FP32 cannot decide
           };
-          for (int m0 = lane; m0 < cnt; m0 += 64) {
-            const int m1 = m0 + 32;
-            const int l0 = lo + m0, l1 = lo + m1;
-            const bool x0 = !B.periodic && (l0 < 0 || l0 >= NTH);
-            const bool x1 = m1 >= cnt || (!B.periodic && (l1 < 0 || l1 >= NTH));
-            const int lw0 = x0 ? 0 : wrapl(l0), lw1 = x1 ? 0 : wrapl(l1);
-            float a0, a1;
-            bool u0 = ray_d2(lw0, &a0);
-            bool u1 = ray_d2(lw1, &a1);
-            float v0 = a0 < rho32 * rho32 ? -a0 : a0;
-            float v1 = a1 < rho32 * rho32 ? -a1 : a1;
-            if (!x0 && u0) {
-              double d64 = ray_distance64<NL>(sh, B, i, lw0);
-              if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
-              float q = (float)(d64 * d64);
-              v0 = d64 < sh.rho ? -q : q;
+          // RPL independent rays per lane and iteration (instruction-level
+          // parallelism for the dependent FP32 chains of the lens map)
+          constexpr int RPL = 2;
+          for (int m0 = lane; m0 < cnt; m0 += 32 * RPL) {
+            float a_[RPL];
+            bool u_[RPL], x_[RPL];
+            int lw_[RPL];
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+              const int m = m0 + 32 * r;
+              const int l = lo + m;
+              x_[r] = m >= cnt || (!B.periodic && (l < 0 || l >= NTH));
+              lw_[r] = x_[r] ? 0 : wrapl(l);
             }
-            if (!x1 && u1) {
-              double d64 = ray_distance64<NL>(sh, B, i, lw1);
-              if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
-              float q = (float)(d64 * d64);
-              v1 = d64 < sh.rho ? -q : q;
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) u_[r] = ray_d2(lw_[r], &a_[r]);
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+              const int m = m0 + 32 * r;
+              float v = a_[r] < rho32 * rho32 ? -a_[r] : a_[r];
+              if (!x_[r] && u_[r]) {
+                double d64 = ray_distance64<NL>(sh, B, i, lw_[r]);
+                if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
+                float q = (float)(d64 * d64);
+                v = d64 < sh.rho ? -q : q;
+              }
+              if (v == 0.f && a_[r] < rho32 * rho32) v = -0.0f;
+              if (m < cnt) buf[m] = x_[r] ? __int_as_float(0x7f800000) : v;
             }
-            if (v0 == 0.f && a0 < rho32 * rho32) v0 = -0.0f;
-            if (v1 == 0.f && a1 < rho32 * rho32) v1 = -0.0f;
-            buf[m0] = x0 ? __int_as_float(0x7f800000) : v0;
-            if (m1 < cnt) buf[m1] = x1 ? __int_as_float(0x7f800000) : v1;
           }
           float* ab = abuf + warp * (seg + 4);
           if (DER)
