@@ -219,6 +219,41 @@ __device__ inline int validate_root64(const Shared& sh, cd z0, cd w, double img_
   return 1;
 }
 
+// Ehrlich-Aberth iteration in FP64 (Sec. 3.1): the fallback for limb points
+// whose FP32 roots give an illegal image count (clusters of close roots next
+// to a critical curve, which FP32 cannot separate).  Stops when every step is
+// below 1e-14 max(1, |z|) or twice the FP64 rounding level of P at the root.
+template <int N>
+__device__ inline int ehrlich_aberth_f64(const cd* b, cd* z, int max_iter) {
+  double ab[N + 1];
+  for (int l = 0; l <= N; ++l) ab[l] = sqrt(abs2(b[l]));
+  for (int it = 0; it < max_iter; ++it) {
+    cd dz[N];
+    double noise[N];
+    bool done = true;
+    for (int k = 0; k < N; ++k) {
+      cd p, dp;
+      horner2<N, double>(b, z[k], p, dp);
+      double az = sqrt(abs2(z[k])), pa = ab[N];
+      for (int l = N - 1; l >= 0; --l) pa = fma(pa, az, ab[l]);
+      noise[k] = 1.1102230246251565e-16 * pa / fmax(sqrt(abs2(dp)), 1e-300);
+      cd W = dv(p, dp);
+      cd S = mk(0.0, 0.0);
+      for (int j = 0; j < N; ++j)
+        if (j != k) S = S + inv(z[k] - z[j]);
+      dz[k] = dv(W, mk(1.0, 0.0) - W * S);
+      if (!(abs2(p) > 0.0)) dz[k] = mk(0.0, 0.0);
+    }
+    for (int k = 0; k < N; ++k) {
+      z[k] = z[k] - dz[k];
+      double st = sqrt(abs2(dz[k]));
+      if (!(st <= fmax(1e-14 * fmax(1.0, sqrt(abs2(z[k]))), 2.0 * noise[k]))) done = false;
+    }
+    if (done) return it + 1;
+  }
+  return -1;
+}
+
 // FP64 distance of ray (i, l) of a sector from the source centre, with the
 // grid of Sec. 3.3: r_i = r_lo + (i + 1/2) dr, th_l = th_lo + (l + 1/2) dth.
 template <int NL>
@@ -289,6 +324,48 @@ __device__ inline T lagrange_basis(const T* y, int npt, T t, T* l) {
     l[1] = t;
   }
   return d1 + (T(2) * t - T(1)) * d2 + ((T(3) * t - T(6)) * t + T(2)) * d3;
+}
+
+// FP64 re-solve of limb point k (all roots, FP64 Ehrlich-Aberth warm-started
+// from the FP32 roots in the lightest lens's frame, FP64 validation of each
+// root); rewrites the point's slots and returns its image count.  Kept out of
+// line: it runs only for limb points with an illegal FP32 image count.
+template <int NL>
+__device__ __noinline__ int resolve_limb_point64(Shared& sh, int k, int K, int max_iter, double img_tol, int PMAX,
+                                                 cf* phi, float* r32, float* rl32, float* t32, float* e32, short* pidx,
+                                                 uint8_t* meta, double* pr, double* pt) {
+  constexpr int N = NL * NL + 1;
+  const int ll = sh.L.ll;
+  const cd w = limb_point64(sh, k, K);
+  double eps[NL];
+  cd a[NL], D[NL + 1], Ee[NL], b[N + 1], z[N];
+  for (int i2 = 0; i2 < NL; ++i2) { eps[i2] = sh.L.eps[i2]; a[i2] = sh.L.a[i2] - sh.L.a[ll]; }
+  poly_DE<NL, double>(eps, a, D, Ee);
+  lens_poly<NL, double>(eps, a, D, Ee, w - sh.L.a[ll], b);
+  for (int j = 0; j < N; ++j) z[j] = tod(phi[k * N + j]);
+  // separate coincident starts
+  for (int j = 1; j < N; ++j)
+    for (int i2 = 0; i2 < j; ++i2)
+      if (abs2(z[j] - z[i2]) < 1e-20) z[j] = z[j] + mk(1e-7 * (j + 1), 1e-7 * j);
+  if (ehrlich_aberth_f64<N>(b, z, max_iter) < 0) atomicOr(&sh.status, ICRS_ST_NONCONV);
+  int m = 0;
+  for (int j = 0; j < N; ++j) {
+    const int ps = k * N + j;
+    phi[ps] = tof(z[j]);
+    pidx[ps] = -1;
+    uint8_t mm = 0;
+    double r, th;
+    if (validate_root64<NL>(sh, z[j] + sh.L.a[ll], w, img_tol, &r, &th)) {
+      const int pi = atomicAdd(&sh.pn, 1);
+      const float rh = (float)r;
+      r32[ps] = rh; rl32[ps] = (float)(r - (double)rh); t32[ps] = (float)th;
+      if (pi < PMAX) { pr[pi] = r; pt[pi] = th; pidx[ps] = (short)pi; e32[ps] = 0.f; mm = M_VALID | M_EXACT; }
+      else { e32[ps] = 1e-12f; mm = M_VALID; atomicOr(&sh.status, ICRS_ST_OVERFLOW); }
+      ++m;
+    }
+    meta[ps] = mm;
+  }
+  return m;
 }
 
 // ---------------------------------------------------------------- queue
@@ -728,13 +805,31 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     }
     __syncthreads();
     if (tid == 0) sh.qn = 0;
-    // image counts per limb point
+    __syncthreads();
+    // image counts per limb point; an illegal count sends the limb point to
+    // an FP64 root solve (warm-started from its FP32 roots) and FP64
+    // validation of every root
+    auto legal_count = [&](int m) -> bool {
+      return (NL == 2) ? (m == 3 || m == 5) : (m == 4 || m == 6 || m == 8 || m == 10);
+    };
     for (int k = tid; k < K; k += NT) {
       int m = 0;
       for (int j = 0; j < N; ++j) m += (meta[k * N + j] & M_VALID) ? 1 : 0;
-      bool legal = (NL == 2) ? (m == 3 || m == 5) : (m == 4 || m == 6 || m == 8 || m == 10);
-      if (!legal) atomicOr(&sh.status, ICRS_ST_IMGCOUNT);
+      if (!legal_count(m)) q_push(sh, queue, k);
     }
+    __syncthreads();
+    {
+      const int qn = min(sh.qn, QMAX);
+      for (int qi = tid; qi < qn; qi += NT) {
+        const int k = queue[qi];
+        atomicAdd(&sh.cnt[1], 1);
+        const int m = resolve_limb_point64<NL>(sh, k, K, g.max_iter, g.img_tol, PMAX, phi, r32, rl32, t32, e32, pidx,
+                                               meta, pr, pt);
+        if (!legal_count(m)) atomicOr(&sh.status, ICRS_ST_IMGCOUNT);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) sh.qn = 0;
     __syncthreads();
 
     // polish helper: process the queue (points not yet exact)
