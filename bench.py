@@ -289,7 +289,8 @@ def surrogate_bench(args, dev):
     err = (A_gate / Ap - 1.0).abs()
     ps_ok = (st == 0) & (feat[:, 6] >= c_ps)
     ps_err = torch.where(ps_ok, (Aps / Ap - 1.0).abs(), torch.zeros_like(err))
-    est_ok = (st == 0) & (feat[:, 6] >= c_est) & (feat[:, 7].abs() <= b_est) & (Aps <= 10.0)
+    est_ok = ((st == 0) & (feat[:, 6] >= c_est) & (feat[:, 7].abs() <= b_est)
+              & (Aps <= torch.where(feat[:, 4] >= float(np.log10(gate.rho_min)) + 3.0, gate.A_max, gate.A_small)))
     Aest = Aps * torch.exp(feat[:, 7].double() / icrs.TARGET_SCALE)
     est_err = torch.where(est_ok, (Aest / Ap - 1.0).abs(), torch.zeros_like(err))
     t_plain, t_gate = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
@@ -299,7 +300,8 @@ def surrogate_bench(args, dev):
             "train_samples": int(args.sur_train_sets * 2000), "train_epochs": args.sur_epochs,
             "train_s": t_train, "data_s": t_data, "final_loss": losses[-1],
             "gate": {"sigma_max": gate.sigma_max, "mu_max": gate.mu_max, "b_max": gate.b_max,
-                     "caustic_min": gate.caustic_min, "A_max": gate.A_max},
+                     "caustic_min": gate.caustic_min, "A_max": gate.A_max, "rho_min": gate.rho_min,
+                     "A_small": gate.A_small},
             "point_source_only": {"accepted_frac": float(ps_ok.float().mean()), "caustic_min": c_ps,
                                   "max_rel_err": float(ps_err.max())},
             "second_order_estimate_only": {"accepted_frac": float(est_ok.float().mean()), "caustic_min": c_est,

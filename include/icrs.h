@@ -233,8 +233,8 @@ int icrs_magnification_indexed(const icrs_params* p, int S, const double* t, int
  *   features  [n][8] device float (16-byte aligned): (w_c.x, w_c.y, log10 s,
  *             (log10 q + 3)/2, log10 rho + 3, 4 (u1 - 0.55),
  *             clamp(log10 min_j |det J(z_j)|, -6, 1), b), where z_j are the
- *             point-source images at the source centre and at the eight limb
- *             points w_c + rho e^{i pi k / 4}.  The network reads the first 7.
+ *             point-source images at the source centre and at the 32 limb
+ *             points w_c + rho e^{i pi k / 16}.  The network reads the first 7.
  *             b = 1e4 log(1 + f_u (mean_k A_ps(limb k) / A_ps - 1)), with
  *             f_u = (15 - 7 u1) / (10 (3 - u1)), is the second-order
  *             finite-source estimate: the network predicts y - b
@@ -317,8 +317,10 @@ size_t icrs_surrogate_gate_workspace_bytes(int n);
  *   - features[i][6] >= caustic_min;
  *   - exp(s_i / 2) <= sigma_max;
  *   - |mu_i| <= mu_max and |features[i][7]| <= b_max;
- *   - A_ps[i] <= A_max (ICRS itself needs more angular rays for small
- *     sources at high magnification, so those epochs stay with ICRS).
+ *   - A_ps[i] <= A_max, or <= A_small when rho < rho_min (for small
+ *     sources away from the far field, and for all sources at high
+ *     magnification, ICRS itself still moves by ~1e-4 between grid
+ *     refinements, so those epochs stay with ICRS).
  * For an accepted epoch, A[i] = A_ps[i] exp(1e-4 (features[i][7] + mu_i)).  Every other epoch is
  * listed, in increasing order, in routed_idx[0 .. *n_routed) (device outputs)
  * and its A[i] is left for icrs_magnification_indexed.
@@ -327,8 +329,8 @@ size_t icrs_surrogate_gate_workspace_bytes(int n);
  */
 int icrs_surrogate_gate(const float* pred, const float* features, const double* A_ps,
                         const uint32_t* st_ps, int n, float sigma_max, float mu_max,
-                        float b_max, float caustic_min, double A_max, double* A, int32_t* routed_idx,
-                        int32_t* n_routed,
+                        float b_max, float caustic_min, double A_max, float rho_min, double A_small,
+                        double* A, int32_t* routed_idx, int32_t* n_routed,
                         void* workspace, size_t workspace_bytes, void* stream);
 
 /* Message for a return code (static string). */

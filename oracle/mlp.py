@@ -139,8 +139,8 @@ ST_LIMB = 64  # the image count changes between the source centre and a limb poi
 
 def features(p: dict, t, grid: dict):
     """Surrogate features of one parameter set at times t, from the oracle's
-    point-source images at the source centre and at the eight limb points
-    w_c + rho e^{i pi k / 4}: returns (features [n, 8], A_ps [n], status [n]).
+    point-source images at the source centre and at the 32 limb points
+    w_c + rho e^{i pi k / 16}: returns (features [n, 8], A_ps [n], status [n]).
     Feature 6 is log10 of the smallest |det J| over all those images, with
     det J = 1 - |sum_i eps_i / (z - a_i)^2|^2 (Eq. detJ), clamped to [-6, 1];
     status gains ST_LIMB when a limb point's image count differs from the
@@ -159,10 +159,10 @@ def features(p: dict, t, grid: dict):
 
     md = np.array([min_det(z[i, : nimg[i]]) for i in range(len(w))])
     Alimb = np.zeros(len(w))
-    for k in range(8):
-        wl = w + p["rho"] * np.exp(1j * np.pi * k / 4.0)
+    for k in range(32):
+        wl = w + p["rho"] * np.exp(1j * np.pi * k / 16.0)
         Al, nl, zl, sl = oracle.point_source(p, grid, wl)
-        Alimb += Al / 8.0
+        Alimb += Al / 32.0
         for i in range(len(w)):
             md[i] = min(md[i], min_det(zl[i, : nl[i]]))
             if nl[i] != nimg[i] or sl[i]:

@@ -479,7 +479,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   int* queue = (int*)p;          p += sizeof(int) * QMAX;
   Anchor* anch = (Anchor*)p;     p += sizeof(Anchor) * MAXANCH;
   cf* tab = (cf*)p;              p += sizeof(cf) * g.n_theta;
-  const int segmax = DER ? 512 : 1024;  // rays per row segment
+  const int segmax = DER ? 256 : 1024;  // rays per row segment
   const int seg = g.n_theta < segmax ? g.n_theta : segmax;
   float* rowbuf = (float*)p;     p += sizeof(float) * NW * (seg + 4);
   cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
@@ -1940,7 +1940,7 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += 3 * ((NP + 15) & ~(size_t)15);
   b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
   b += sizeof(int) * NW * ((!der && NL == 2 && defer) ? 256 : 64);  // per-warp boundary queues
-  const int segmax = der ? 512 : 1024;
+  const int segmax = der ? 256 : 1024;
   const int seg = g.n_theta < segmax ? g.n_theta : segmax;
   if (der) b += sizeof(DerShared) + sizeof(float) * NW * (seg + 4);  // state and ray seeds
   b += sizeof(cf) * g.n_theta;

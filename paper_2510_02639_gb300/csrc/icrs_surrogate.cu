@@ -459,6 +459,7 @@ __global__ void reduce_adam_kernel(float* __restrict__ theta, float* __restrict_
 
 // ---------------------------------------------------------------- features
 constexpr float TARGET_SCALE = 1e4f;
+constexpr int NLIMB_SG = 32;  // source-limb points of the feature kernel
 
 __global__ void features_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ T, int E,
                                 icrs_grid g, float* __restrict__ feat, double* __restrict__ A_ps,
@@ -470,19 +471,20 @@ __global__ void features_kernel(const icrs_params* __restrict__ P, int S, const 
   const Lens L = make_lens(prm);
   const cd w = source_centre(prm, T[idx]);
   PointSource<2> ps = point_source_solve<2>(L, w, g.max_iter, g.img_tol, nullptr);
-  // eight source-limb points: a caustic inside the disk changes the image
-  // count between the centre and some limb point, which the centre's own
-  // images cannot show when the centre lies outside the caustic
+  // 32 source-limb points: a caustic inside the disk changes the image count
+  // between the centre and some limb point, which the centre's own images
+  // cannot show when the centre lies outside the caustic (a cusp tip can
+  // enter the disk between widely spaced samples)
   double mind = ps.m > 0 ? ps.min_det : 0.0;
   uint32_t stf = ps.st;
   double Alimb = 0.0;
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < NLIMB_SG; ++k) {
     double sn, cs;
-    sincospi(0.25 * k, &sn, &cs);
+    sincospi(2.0 * k / NLIMB_SG, &sn, &cs);
     PointSource<2> pl = point_source_solve<2>(L, mk(w.x + prm.rho * cs, w.y + prm.rho * sn), g.max_iter, g.img_tol, nullptr);
     mind = fmin(mind, pl.m > 0 ? pl.min_det : 0.0);
     if (pl.m != ps.m || pl.st) stf |= ICRS_ST_LIMB;
-    Alimb += 0.125 * pl.A;
+    Alimb += pl.A / NLIMB_SG;
   }
   // second-order finite-source estimate: the limb mean minus the centre is
   // (rho^2 / 4) lap A to leading order, and the disk average of A is
@@ -507,16 +509,17 @@ __global__ void features_kernel(const icrs_params* __restrict__ P, int S, const 
 // Accept an epoch when its point-source solve is clean, its caustic feature
 // is at least caustic_min, the predicted standard deviation exp(s/2) is at
 // most sigma_max, |mu| at most mu_max, the second-order estimate |b|
-// (feature 7) at most b_max (units of 1e-4 in log A) and A_ps at most A_max
-// (small sources at high magnification are where ICRS itself needs more
-// angular rays); accepted epochs get
+// (feature 7) at most b_max (units of 1e-4 in log A), and A_ps at most A_max
+// (A_small when rho < rho_min: small sources away from the far field, and all
+// sources at high magnification, are where ICRS itself still moves by 1e-4
+// between grid refinements); accepted epochs get
 // A = A_ps exp(1e-4 (b + mu)).  Routed epochs are listed in order.
 constexpr int GB = 1024;  // queries per gate block
 
 __global__ void gate_flags_kernel(const float* __restrict__ pred, const float* __restrict__ feat,
                                   const double* __restrict__ A_ps, const uint32_t* __restrict__ st_ps, int n,
                                   float sigma_max, float mu_max, float b_max, float caustic_min, double A_max,
-                                  double* __restrict__ A,
+                                  float rho_min, double A_small, double* __restrict__ A,
                                   uint8_t* __restrict__ flag, int32_t* __restrict__ bcount) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
@@ -527,7 +530,8 @@ __global__ void gate_flags_kernel(const float* __restrict__ pred, const float* _
     const float mu = pred[(size_t)q * 2], s = pred[(size_t)q * 2 + 1];
     const float base = feat[(size_t)q * 8 + 7];
     const bool ok = st_ps[q] == 0u && feat[(size_t)q * 8 + 6] >= caustic_min && expf(0.5f * s) <= sigma_max &&
-                    fabsf(mu) <= mu_max && fabsf(base) <= b_max && isfinite(mu) && A_ps[q] <= A_max;
+                    fabsf(mu) <= mu_max && fabsf(base) <= b_max && isfinite(mu) &&
+                    A_ps[q] <= (feat[(size_t)q * 8 + 4] >= log10f(rho_min) + 3.0f ? A_max : A_small);
     routed = ok ? 0 : 1;
     if (ok) A[q] = A_ps[q] * exp(((double)base + (double)mu) / (double)TARGET_SCALE);
     flag[q] = (uint8_t)routed;
@@ -708,8 +712,8 @@ size_t icrs_surrogate_gate_workspace_bytes(int n) {
 }
 
 int icrs_surrogate_gate(const float* pred, const float* feat, const double* A_ps, const uint32_t* st_ps, int n,
-                        float sigma_max, float mu_max, float b_max, float caustic_min, double A_max, double* A,
-                        int32_t* routed_idx,
+                        float sigma_max, float mu_max, float b_max, float caustic_min, double A_max, float rho_min,
+                        double A_small, double* A, int32_t* routed_idx,
                         int32_t* n_routed, void* workspace, size_t workspace_bytes, void* stream) {
   if (n < 0) return ICRS_EINVAL;
   if (n == 0) return ICRS_OK;
@@ -719,8 +723,8 @@ int icrs_surrogate_gate(const float* pred, const float* feat, const double* A_ps
   const int nb = (n + GB - 1) / GB;
   uint8_t* flag = (uint8_t*)workspace;
   int32_t* bcount = (int32_t*)((uint8_t*)workspace + ((size_t)n + 255) / 256 * 256);
-  gate_flags_kernel<<<nb, GB, 0, st>>>(pred, feat, A_ps, st_ps, n, sigma_max, mu_max, b_max, caustic_min, A_max, A,
-                                       flag, bcount);
+  gate_flags_kernel<<<nb, GB, 0, st>>>(pred, feat, A_ps, st_ps, n, sigma_max, mu_max, b_max, caustic_min, A_max,
+                                       rho_min, A_small, A, flag, bcount);
   gate_scan_kernel<<<1, 1024, 0, st>>>(bcount, nb, n_routed);
   gate_scatter_kernel<<<nb, GB, 0, st>>>(flag, n, bcount, routed_idx);
   return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;

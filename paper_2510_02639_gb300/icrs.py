@@ -106,7 +106,8 @@ def _load():
     L.icrs_surrogate_gate_workspace_bytes.argtypes = [ctypes.c_int]
     L.icrs_surrogate_gate_workspace_bytes.restype = ctypes.c_size_t
     L.icrs_surrogate_gate.argtypes = [vp, vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
-                                      ctypes.c_float, ctypes.c_double, vp, vp, vp, vp, ctypes.c_size_t, vp]
+                                      ctypes.c_float, ctypes.c_double, ctypes.c_float, ctypes.c_double, vp, vp, vp, vp,
+                                      ctypes.c_size_t, vp]
     L.icrs_surrogate_gate.restype = ctypes.c_int
     L.icrs_strerror.argtypes = [ctypes.c_int]
     L.icrs_strerror.restype = ctypes.c_char_p
@@ -368,8 +369,8 @@ def surrogate_features(params_dev, t, grid: IcrsGrid, stream=None):
     return feat, Aps, st
 
 
-def surrogate_gate(pred, feat, A_ps, st_ps, sigma_max, mu_max, b_max, caustic_min, A_max=1e300, A=None,
-                   stream=None):
+def surrogate_gate(pred, feat, A_ps, st_ps, sigma_max, mu_max, b_max, caustic_min, A_max=1e300, rho_min=0.0,
+                   A_small=1e300, A=None, stream=None):
     """Returns (A [n] f64 with accepted epochs filled, routed_idx [n] int32,
     n_routed [1] int32 device)."""
     import torch
@@ -381,7 +382,8 @@ def surrogate_gate(pred, feat, A_ps, st_ps, sigma_max, mu_max, b_max, caustic_mi
     nr = torch.zeros((1,), dtype=torch.int32, device=dev)
     ws = torch.empty(max(int(lib.icrs_surrogate_gate_workspace_bytes(n)), 256), dtype=torch.uint8, device=dev)
     check(lib.icrs_surrogate_gate(_ptr(pred), _ptr(feat), _ptr(A_ps), _ptr(st_ps), n, float(sigma_max),
-                                  float(mu_max), float(b_max), float(caustic_min), float(A_max), _ptr(A), _ptr(idx),
+                                  float(mu_max), float(b_max), float(caustic_min), float(A_max), float(rho_min),
+                                  float(A_small), _ptr(A), _ptr(idx),
                                   _ptr(nr), _ptr(ws),
                                   ws.numel(), _stream(torch, stream)))
     return A, idx, nr

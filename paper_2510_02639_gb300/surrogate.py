@@ -8,12 +8,12 @@ calibrates the gate.
 
 Target: y = 1e4 log(A_ICRS / A_ps) minus b, the second-order finite-source
 estimate of the feature kernel (features[:, 7]: the disk average of the
-point-source magnification from its eight limb values and the limb-darkening
+point-source magnification from its 32 limb values and the limb-darkening
 law's second moment).  Prediction: A = A_ps exp(1e-4 (b + mu)).
 Gate: an epoch is accepted when its point-source solves are clean (no caustic
 inside the disk), its caustic feature is >= caustic_min, the predicted
-standard deviation exp(s / 2) is <= sigma_max, |mu| <= mu_max, |b| <= b_max
-and A_ps <= A_max.
+standard deviation exp(s / 2) is <= sigma_max, |mu| <= mu_max, |b| <= b_max,
+and A_ps <= A_max (A_small when rho < rho_min).
 Everything else runs through ICRS.
 """
 from __future__ import annotations
@@ -125,7 +125,7 @@ class Surrogate:
             feat, A_ps, st = icrs.surrogate_features(params_dev, t, grid)
         pred = self.predict(feat)
         A, idx, nr = icrs.surrogate_gate(pred, feat, A_ps, st, gate.sigma_max, gate.mu_max, gate.b_max,
-                                         gate.caustic_min, gate.A_max)
+                                         gate.caustic_min, gate.A_max, gate.rho_min, gate.A_small)
         k = int(nr.item())
         if k:
             icrs.magnification_indexed(params_dev, t, grid, idx, k, A)
@@ -139,16 +139,22 @@ class Gate:
     b_max: float
     caustic_min: float
     A_max: float
+    rho_min: float
+    A_small: float
 
 
 def calibrate(sur: Surrogate, val: Dataset, tol: float = 1e-4, margin: float = 2.0, mu_max: float = 2.0,
-              b_max: float = 10.0, caustic_min: float = -1.0, A_max: float = 10.0) -> Gate:
+              b_max: float = 10.0, caustic_min: float = -1.0, A_max: float = 10.0, rho_min: float = 5e-4,
+              A_small: float = 2.0) -> Gate:
     """Gate thresholds.  The physical ones are fixed:
       - |b| <= 10 (the second-order estimate within 1e-3, so its neglected
         higher orders are ~1e-6);
       - |mu| <= 2 (the network corrects the estimate only slightly);
       - min |det J| >= 0.1 over the nine point-source solves;
-      - A_ps <= 10.
+      - A_ps <= 10, and A_ps <= 2 when rho < 5e-4 (small sources away from
+        the far field, and all sources at high magnification, are where
+        ICRS at the headline grid itself still moves by 1e-4 between grid
+        refinements, so no surrogate can track it to 1e-4).
     sigma_max is the largest value at which every accepted validation epoch
     stays within tol / margin of ICRS."""
     import torch
@@ -158,12 +164,12 @@ def calibrate(sur: Surrogate, val: Dataset, tol: float = 1e-4, margin: float = 2
     b = val.feat[:, 7].double()
     err = (val.A_ps * torch.exp((b + mu) / icrs.TARGET_SCALE) / val.A - 1.0).abs()
     base = ((val.st == 0) & (val.feat[:, 6] >= caustic_min) & (mu.abs() <= mu_max) & (b.abs() <= b_max)
-            & (val.A_ps <= A_max))
+            & (val.A_ps <= torch.where(val.feat[:, 4] >= float(np.log10(rho_min)) + 3.0, A_max, A_small)))
     order = torch.argsort(sig)
     e_sorted = torch.where(base[order], err[order], torch.zeros_like(err))
     good = torch.cummax(e_sorted, 0).values <= tol / margin
     smax = float(sig[order][int(torch.nonzero(good).max().item())].item()) if bool(good[0]) else 0.0
-    return Gate(smax, mu_max, b_max, caustic_min, A_max)
+    return Gate(smax, mu_max, b_max, caustic_min, A_max, rho_min, A_small)
 
 
 def calibrate_point_source(val: Dataset, tol: float = 1e-4, margin: float = 2.0, use_estimate: bool = False):
@@ -187,7 +193,8 @@ def calibrate_point_source(val: Dataset, tol: float = 1e-4, margin: float = 2.0,
 
 def calibrate_estimate(val: Dataset, tol: float = 1e-4, margin: float = 2.0,
                        caustic_grid=(-6.0, -3.0, -2.0, -1.5, -1.0, -0.5, 0.0),
-                       b_grid=(1.0, 3.0, 10.0, 30.0, 100.0, 300.0), A_max: float = 10.0):
+                       b_grid=(1.0, 3.0, 10.0, 30.0, 100.0, 300.0), A_max: float = 10.0, rho_min: float = 5e-4,
+                       A_small: float = 2.0):
     """The second-order estimate without the network, A = A_ps exp(1e-4 b),
     with the same A_ps <= A_max cut: the (caustic_min, b_max) that accepts
     the most validation epochs while all of them stay within tol / margin.
@@ -198,7 +205,8 @@ def calibrate_estimate(val: Dataset, tol: float = 1e-4, margin: float = 2.0,
     best, best_n = (2.0, 0.0), -1
     for c in caustic_grid:
         for bm in b_grid:
-            sel = (val.st == 0) & (val.feat[:, 6] >= c) & (b.abs() <= bm) & (val.A_ps <= A_max)
+            sel = ((val.st == 0) & (val.feat[:, 6] >= c) & (b.abs() <= bm)
+                   & (val.A_ps <= torch.where(val.feat[:, 4] >= float(np.log10(rho_min)) + 3.0, A_max, A_small)))
             n = int(sel.sum().item())
             if n > best_n and (n == 0 or float(err[sel].max()) <= tol / margin):
                 best, best_n = (float(c), float(bm)), n

@@ -108,6 +108,17 @@ def test_dA_uniform_and_grid_variants(G, oracle_mod):
         assert_dA(dA, dAo, str(g), Ao)
 
 
+def test_dA_fine_grid(G, oracle_mod):
+    """Derivative mode on a finer grid (128 x 1024: rows of four segments)."""
+    params, t = I.caustic_crossing_binary(n_epochs=40)
+    t = t[:, ::4]
+    g = I.grid(n_r=128, n_theta=1024)
+    A, dA, st, _ = gpu_dA(G, params, t, g)
+    Ao, dAo, so = oracle_mod.magnification_fwd(params, t, g)
+    assert np.all(np.abs(A / Ao - 1) <= 1e-5)
+    assert_dA(dA, dAo, "128x1024", Ao)
+
+
 def test_vjp_and_chi2_against_oracle(G, oracle_mod):
     """grad = sum_e gA_e dA_e for a random upstream gA; chi^2 and its gradient
     against the oracle's A and dA."""

@@ -197,7 +197,7 @@ def test_surrogate_gain_over_plain_icrs(G):
     ps_err = torch.where(ps_ok, (test.A_ps / test.A - 1.0).abs(), torch.zeros_like(err))
     c_est, b_est = SG.calibrate_estimate(val)
     est_ok = ((test.st == 0) & (test.feat[:, 6] >= c_est) & (test.feat[:, 7].abs() <= b_est)
-              & (test.A_ps <= 10.0))
+              & (test.A_ps <= torch.where(test.feat[:, 4] >= float(np.log10(5e-4)) + 3.0, 10.0, 2.0)))
     est_err = torch.where(est_ok, (test.A_ps * torch.exp(test.feat[:, 7].double() * 1e-4) / test.A - 1.0).abs(),
                           torch.zeros_like(err))
     print(f"losses {losses[0]:.3f} -> {losses[-1]:.3f}; gate {gate}; "

@@ -100,7 +100,7 @@ def test_ld_second_moment_closed_form():
 
 def test_second_order_estimate_single_lens(oracle_mod):
     """Far single lens (q = 1e-9, s = 50): the second-order finite-source
-    estimate b from the eight limb point-source magnifications reproduces the
+    estimate b from the 32 limb point-source magnifications reproduces the
     closed-form limb-darkened disk magnification to O((rho/u)^4)."""
     from tests import closed_forms as CF
     from paper_2510_02639_gb300 import inputs as I
