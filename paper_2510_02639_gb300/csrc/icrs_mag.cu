@@ -49,6 +49,15 @@ constexpr int MAXBOX_D = 32;     // candidate sectors with tracked derivatives
 constexpr float TINY_EXTENT = 3e-4f;  // images smaller than this x rho skip FP64 decisions
 constexpr float EPS32 = 5.9604645e-8f;  // 2^-24
 
+// Rays per row segment.  Forward: 508, so that a segment and its 4-ray halo
+// fill exactly 8 iterations of 32 lanes x 2 rays; the row buffers then leave
+// room for an FP64 point table that holds every image-limb point at n_theta
+// = 2048.  Derivative mode: 256 (its per-ray seeds take the same room again).
+__host__ __device__ __forceinline__ int row_segment(int n_theta, bool der) {
+  const int segmax = der ? 256 : 508;
+  return n_theta < segmax ? n_theta : segmax;
+}
+
 // Meta bits of an image-limb slot.
 constexpr uint8_t M_VALID = 1, M_EXACT = 2, M_UNSURE = 4, M_CAND = 8;
 
@@ -479,8 +488,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   int* queue = (int*)p;          p += sizeof(int) * QMAX;
   Anchor* anch = (Anchor*)p;     p += sizeof(Anchor) * MAXANCH;
   cf* tab = (cf*)p;              p += sizeof(cf) * g.n_theta;
-  const int segmax = DER ? 256 : 1024;  // rays per row segment
-  const int seg = g.n_theta < segmax ? g.n_theta : segmax;
+  const int seg = row_segment(g.n_theta, DER);  // rays per row segment
   float* rowbuf = (float*)p;     p += sizeof(float) * NW * (seg + 4);
   cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
   // boundary points of the current row segment; forward binary mode: a
@@ -1940,8 +1948,7 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += 3 * ((NP + 15) & ~(size_t)15);
   b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
   b += sizeof(int) * NW * ((!der && NL == 2 && defer) ? 256 : 64);  // per-warp boundary queues
-  const int segmax = der ? 256 : 1024;
-  const int seg = g.n_theta < segmax ? g.n_theta : segmax;
+  const int seg = row_segment(g.n_theta, der);
   if (der) b += sizeof(DerShared) + sizeof(float) * NW * (seg + 4);  // state and ray seeds
   b += sizeof(cf) * g.n_theta;
   b += sizeof(float) * NW * (seg + 4);
@@ -1976,7 +1983,7 @@ static int first_n_lens(const icrs_params* p, cudaStream_t st, int* nl) {
 }
 
 // Launch of one instantiation: shared-memory sizing (the FP64 point table
-// takes what is left, up to 2048 entries), occupancy, contiguous chunks of
+// takes what is left, up to one entry per image-limb slot), occupancy, contiguous chunks of
 // epochs per block (warm starts along the light curve).
 template <int NL, bool DER>
 static int launch_inst(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, double* A,
@@ -1987,18 +1994,22 @@ static int launch_inst(const icrs_params* p, int S, const double* t, int E, cons
   int optin = 0, nsm = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return ICRS_ECUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ICRS_ECUDA;
-  // shared memory: the deferred boundary queue (binary forward) if it fits,
-  // then the lo parts of image positions if they fit, then the FP64 point
-  // table grows to at most 2048 entries
+  // shared memory: the deferred boundary queue (binary forward) if it fits;
+  // then, forward, the FP64 point table grows (up to one entry per
+  // image-limb slot) before the lo parts of image positions are added;
+  // derivative mode takes the lo parts first (fewer FP64 polishes)
   auto fits = [&](int pm, int plo, int df) {
     return mag_smem_bytes(NL, *g, pm, plo, DER, df) + sizeof(Shared) <= (size_t)optin;
   };
   int pmax = PMAX_MIN;
   int defer = (NL == 2 && !DER) ? 1 : 0;
   if (!fits(pmax, 0, defer)) defer = 0;
-  int has_plo = fits(pmax, 1, defer) ? 1 : 0;
-  if (!fits(pmax, has_plo, defer)) return ICRS_EUNSUPPORTED;
-  while (pmax < 2048 && fits(pmax * 2, has_plo, defer)) pmax *= 2;
+  if (!fits(pmax, 0, defer)) return ICRS_EUNSUPPORTED;
+  int has_plo = (DER && fits(pmax, 1, defer)) ? 1 : 0;
+  const int np_all = g->n_limb * (NL * NL + 1);
+  while (pmax < np_all && fits(pmax * 2 < np_all ? pmax * 2 : np_all, has_plo, defer))
+    pmax = pmax * 2 < np_all ? pmax * 2 : np_all;
+  if (!DER) has_plo = fits(pmax, 1, defer) ? 1 : 0;
   size_t smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER, defer);
   if (cudaFuncSetAttribute(mag_kernel<NL, DER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return ICRS_ECUDA;
