@@ -278,15 +278,24 @@ def surrogate_bench(args, dev):
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
     e[0].record()
-    A_plain, _ = icrs.magnification(pd, tt, g)
+    A_plain, st_plain = icrs.magnification(pd, tt, g)
     e[1].record()
-    A_gate, k = sur.gated_magnification(pd, tt, g, gate)
+    A_gate, k, idx = sur.gated_magnification(pd, tt, g, gate, return_index=True)
     e[2].record()
     torch.cuda.synchronize()
     feat, Aps, st = icrs.surrogate_features(pd, tt, g)
     n = A_gate.numel()
     Ap = A_plain.reshape(-1)
     err = (A_gate / Ap - 1.0).abs()
+    routed = torch.zeros(n, dtype=torch.bool, device=dev)
+    routed[idx.long()] = True
+    # plain ICRS epochs that flag themselves (non-converged roots, illegal
+    # image count, merged sectors, grid edge, NaN)
+    flagged = (st_plain.reshape(-1) & 0x1F) != 0
+
+    def err_stats(mask):
+        em = torch.where(mask, err, torch.zeros_like(err))
+        return {"n": int(mask.sum()), "max_rel_err": float(em.max()), "n_above_1e-4": int((em > 1e-4).sum())}
     ps_ok = (st == 0) & (feat[:, 6] >= c_ps)
     ps_err = torch.where(ps_ok, (Aps / Ap - 1.0).abs(), torch.zeros_like(err))
     est_ok = ((st == 0) & (feat[:, 6] >= c_est) & (feat[:, 7].abs() <= b_est)
@@ -295,7 +304,13 @@ def surrogate_bench(args, dev):
     est_err = torch.where(est_ok, (Aest / Ap - 1.0).abs(), torch.zeros_like(err))
     t_plain, t_gate = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
     return {"speedup": t_plain / t_gate, "queries": n, "routed_frac": k / n,
-            "max_rel_err_vs_plain": float(err.max()), "plain_ms": t_plain, "gated_ms": t_gate,
+            "max_rel_err_vs_plain": float(err.max()),
+            "vs_plain": {"accepted": err_stats(~routed), "routed_plain_unflagged": err_stats(routed & ~flagged),
+                         "routed_plain_flagged": err_stats(routed & flagged),
+                         "note": "accepted: surrogate vs ICRS at this grid (ICRS itself under-resolves a sector "
+                                 "holding two images in adjacent theta bins); routed: the indexed ICRS launch vs "
+                                 "the full launch (warm starts differ; flagged epochs merged sectors)"},
+            "plain_ms": t_plain, "gated_ms": t_gate,
             "gated_magnifications_per_s": n / t_gate * 1e3, "grid": grid_desc(gd),
             "train_samples": int(args.sur_train_sets * 2000), "train_epochs": args.sur_epochs,
             "train_s": t_train, "data_s": t_data, "final_loss": losses[-1],

@@ -50,6 +50,11 @@ extern "C" {
 #define ICRS_ST_NAN 16u      /* non-finite result */
 #define ICRS_ST_OVERFLOW 32u /* an on-chip table overflowed; a decision was taken in FP32 */
 #define ICRS_ST_LIMB 64u     /* surrogate features: the image count changes across the source disk */
+#define ICRS_ST_ROUGH 128u   /* surrogate features: the limb magnification varies on the source's scale */
+/* Threshold of ICRS_ST_ROUGH: the angular harmonics of order >= 3 of A_ps
+ * along the 32 limb points, summed in magnitude over both signs of the order,
+ * relative to A_ps at the centre. */
+#define ICRS_ROUGH_MAX 1e-3
 /* icrs_magnification also stores the number of sectors integrated for the
  * epoch in bits 8..15 of its status word. */
 #define ICRS_ST_NSECT(st) (((st) >> 8) & 0xffu)
@@ -302,7 +307,12 @@ int icrs_mlp_train_step_noalloc(float* theta, float* adam_m, float* adam_v, void
  *   A_ps      [S][E] device double (out): point-source magnification
  *   status    [S][E] device uint32 or NULL (out): the point-source ICRS_ST_* bits
  *             of the centre and limb solves, plus ICRS_ST_LIMB when a limb
- *             point has a different image count from the centre
+ *             point has a different image count from the centre, plus
+ *             ICRS_ST_ROUGH when H > ICRS_ROUGH_MAX (or H is not finite), with
+ *             H = (1/32) sum_{m=3..29} |sum_k (A_k - A_c) e^{-2 pi i m k / 32}| / A_c
+ *             over the limb magnifications A_k at w_c + rho e^{2 pi i k / 32}:
+ *             structure on the scale of the source (a caustic a few rho
+ *             away) that the second-order estimate of feature 7 misses
  */
 int icrs_surrogate_features(const icrs_params* p, int S, const double* t, int E,
                             const icrs_grid* g, float* features, double* A_ps,
@@ -313,7 +323,8 @@ size_t icrs_surrogate_gate_workspace_bytes(int n);
 
 /*
  * Error gate.  Epoch i is accepted when all of these hold:
- *   - its point-source status is 0;
+ *   - its feature status is 0 (clean solves, the same image count across
+ *     the disk, and no ICRS_ST_ROUGH);
  *   - features[i][6] >= caustic_min;
  *   - exp(s_i / 2) <= sigma_max;
  *   - |mu_i| <= mu_max and |features[i][7]| <= b_max;

@@ -135,16 +135,30 @@ def adam(theta, m, v, grad, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 ST_LIMB = 64  # the image count changes between the source centre and a limb point
+ST_ROUGH = 128  # the limb magnification varies on the scale of the source (limb_roughness > ROUGH_MAX)
+ROUGH_MAX = 1e-3
 
 
-def features(p: dict, t, grid: dict):
+def limb_roughness(A_c, A_limb):
+    """H = (1/32) sum_{m=3..29} |sum_k (A_k - A_c) e^{-2 pi i m k / 32}| / A_c:
+    the angular harmonics of order >= 3 (both signs) of the limb
+    magnifications A_limb [n, 32] relative to the centre's A_c [n].  A
+    magnification field that is smooth on the source's scale has harmonics
+    that fall off like (rho / L)^m; a caustic a few rho away raises them."""
+    d = A_limb - A_c[:, None]
+    c = np.fft.fft(d, axis=1)
+    return np.sum(np.abs(c[:, 3:30]), axis=1) / 32.0 / A_c
+
+
+def features(p: dict, t, grid: dict, return_roughness: bool = False):
     """Surrogate features of one parameter set at times t, from the oracle's
     point-source images at the source centre and at the 32 limb points
-    w_c + rho e^{i pi k / 16}: returns (features [n, 8], A_ps [n], status [n]).
+    w_c + rho e^{i pi k / 16}: returns (features [n, 8], A_ps [n], status [n]),
+    and H of limb_roughness when return_roughness is set.
     Feature 6 is log10 of the smallest |det J| over all those images, with
     det J = 1 - |sum_i eps_i / (z - a_i)^2|^2 (Eq. detJ), clamped to [-6, 1];
     status gains ST_LIMB when a limb point's image count differs from the
-    centre's."""
+    centre's, and ST_ROUGH when H > ROUGH_MAX or H is not finite."""
     import oracle
     w = oracle.source_centre(p, t)
     A, nimg, z, st = oracle.point_source(p, grid, w)
@@ -159,10 +173,12 @@ def features(p: dict, t, grid: dict):
 
     md = np.array([min_det(z[i, : nimg[i]]) for i in range(len(w))])
     Alimb = np.zeros(len(w))
+    Ak = np.zeros((len(w), 32))
     for k in range(32):
         wl = w + p["rho"] * np.exp(1j * np.pi * k / 16.0)
         Al, nl, zl, sl = oracle.point_source(p, grid, wl)
         Alimb += Al / 32.0
+        Ak[:, k] = Al
         for i in range(len(w)):
             md[i] = min(md[i], min_det(zl[i, : nl[i]]))
             if nl[i] != nimg[i] or sl[i]:
@@ -173,10 +189,15 @@ def features(p: dict, t, grid: dict):
     u = p["u1"]
     fu = (15.0 - 7.0 * u) / (10.0 * (3.0 - u))
     base = 1e4 * np.log1p(fu * (Alimb / A - 1.0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rough = limb_roughness(A, Ak)
+    st[~(rough <= ROUGH_MAX)] |= np.uint32(ST_ROUGH)
     out = np.zeros((len(w), 8))
     for i in range(len(w)):
         lg = np.log10(md[i]) if md[i] > 0 else -np.inf
         out[i] = [w[i].real, w[i].imag, np.log10(p["s"]), (np.log10(p["q"]) + 3.0) / 2.0,
                   np.log10(p["rho"]) + 3.0, 4.0 * (p["u1"] - 0.55), min(1.0, max(-6.0, lg)),
                   min(1e4, max(-1e4, base[i]))]
+    if return_roughness:
+        return out, A, st, rough
     return out, A, st

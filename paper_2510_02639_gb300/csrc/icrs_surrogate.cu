@@ -460,10 +460,22 @@ __global__ void reduce_adam_kernel(float* __restrict__ theta, float* __restrict_
 // ---------------------------------------------------------------- features
 constexpr float TARGET_SCALE = 1e4f;
 constexpr int NLIMB_SG = 32;  // source-limb points of the feature kernel
+constexpr int FEAT_THREADS = 128;  // threads (epochs) per feature block
+static_assert((NLIMB_SG & (NLIMB_SG - 1)) == 0, "the harmonic index wraps with a mask");
 
 __global__ void features_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ T, int E,
                                 icrs_grid g, float* __restrict__ feat, double* __restrict__ A_ps,
                                 uint32_t* __restrict__ status) {
+  // limb magnifications minus the centre's, [k][thread], and the twiddles
+  // e^{-2 pi i j / 32} of the limb harmonics
+  __shared__ float dlimb[NLIMB_SG][FEAT_THREADS];
+  __shared__ float2 tw[NLIMB_SG];
+  if (threadIdx.x < NLIMB_SG) {
+    double sn, cs;
+    sincospi(2.0 * threadIdx.x / NLIMB_SG, &sn, &cs);
+    tw[threadIdx.x] = make_float2((float)cs, (float)-sn);
+  }
+  __syncthreads();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)S * E) return;
   const int s = (int)(idx / E);
@@ -485,7 +497,23 @@ __global__ void features_kernel(const icrs_params* __restrict__ P, int S, const 
     mind = fmin(mind, pl.m > 0 ? pl.min_det : 0.0);
     if (pl.m != ps.m || pl.st) stf |= ICRS_ST_LIMB;
     Alimb += pl.A / NLIMB_SG;
+    dlimb[k][threadIdx.x] = (float)(pl.A - ps.A);
   }
+  // harmonics of order m = 3..16 of the limb values (the orders 17..29 are
+  // their mirror images, so orders 3..15 count twice and 16 once)
+  float hsum = 0.f;
+  for (int m = 3; m <= NLIMB_SG / 2; ++m) {
+    float cr = 0.f, ci = 0.f;
+    for (int k = 0; k < NLIMB_SG; ++k) {
+      const float2 w_ = tw[(m * k) & (NLIMB_SG - 1)];
+      const float d = dlimb[k][threadIdx.x];
+      cr = fmaf(d, w_.x, cr);
+      ci = fmaf(d, w_.y, ci);
+    }
+    hsum += (m < NLIMB_SG / 2 ? 2.f : 1.f) * sqrtf(cr * cr + ci * ci);
+  }
+  const double rough = (double)hsum / NLIMB_SG / ps.A;
+  if (!(rough <= ICRS_ROUGH_MAX)) stf |= ICRS_ST_ROUGH;
   // second-order finite-source estimate: the limb mean minus the centre is
   // (rho^2 / 4) lap A to leading order, and the disk average of A is
   // A + (<r^2> / 4) lap A with <r^2> / rho^2 = (15 - 7 u) / (10 (3 - u)) for
@@ -506,7 +534,8 @@ __global__ void features_kernel(const icrs_params* __restrict__ P, int S, const 
 }
 
 // ---------------------------------------------------------------- gate
-// Accept an epoch when its point-source solve is clean, its caustic feature
+// Accept an epoch when its feature status is clean (solves, image count across
+// the disk, limb roughness), its caustic feature
 // is at least caustic_min, the predicted standard deviation exp(s/2) is at
 // most sigma_max, |mu| at most mu_max, the second-order estimate |b|
 // (feature 7) at most b_max (units of 1e-4 in log A), and A_ps at most A_max
@@ -699,9 +728,9 @@ int icrs_surrogate_features(const icrs_params* p, int S, const double* t, int E,
   if (!p || !t || !feat || !A_ps) return ICRS_EINVAL;
   if (g->n_lens != 2) return ICRS_EUNSUPPORTED;
   const long long total = (long long)S * E;
-  const long long blocks = (total + 127) / 128;
+  const long long blocks = (total + FEAT_THREADS - 1) / FEAT_THREADS;
   if (blocks > 2147483647LL) return ICRS_EUNSUPPORTED;
-  features_kernel<<<(unsigned)blocks, 128, 0, (cudaStream_t)stream>>>(p, S, t, E, *g, feat, A_ps, status);
+  features_kernel<<<(unsigned)blocks, FEAT_THREADS, 0, (cudaStream_t)stream>>>(p, S, t, E, *g, feat, A_ps, status);
   return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
 }
 

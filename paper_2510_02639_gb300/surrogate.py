@@ -117,10 +117,12 @@ class Surrogate:
     def predict(self, feat):
         return icrs.mlp_infer(self.pack, self.theta, feat, err=self.err)
 
-    def gated_magnification(self, params_dev, t, grid, gate, feat=None, A_ps=None, st=None):
+    def gated_magnification(self, params_dev, t, grid, gate, feat=None, A_ps=None, st=None,
+                            return_index=False):
         """A [S * E] through the gate (a Gate from calibrate()): accepted
         epochs from the surrogate, routed epochs from ICRS.  Returns (A,
-        number routed)."""
+        number routed), and the routed indices (items s * E + e, the first
+        k entries) when return_index is set."""
         if feat is None:
             feat, A_ps, st = icrs.surrogate_features(params_dev, t, grid)
         pred = self.predict(feat)
@@ -129,7 +131,7 @@ class Surrogate:
         k = int(nr.item())
         if k:
             icrs.magnification_indexed(params_dev, t, grid, idx, k, A)
-        return A, k
+        return (A, k, idx[:k]) if return_index else (A, k)
 
 
 @dataclass
@@ -143,20 +145,41 @@ class Gate:
     A_small: float
 
 
+# Validation labels are ICRS at the headline grid, which is itself off by
+# 1e-4 to 1e-2 on rare epochs (a sector shared by two images, small sources
+# at moderate magnification).  No smooth model can predict those labels, so
+# each calibration below tolerates up to EXCEED_FRAC exceedances per accepted
+# validation epoch instead of none.
+EXCEED_FRAC = 1e-4
+
+
+def _loosest_prefix(ok_sorted, err_sorted, thr: float, frac: float) -> int:
+    """Largest i such that, among the first i + 1 entries with ok_sorted set,
+    at most floor(frac x their number) have err_sorted > thr; -1 if none."""
+    import torch
+    ok = ok_sorted.to(torch.int64)
+    n_ok = torch.cumsum(ok, 0)
+    n_bad = torch.cumsum(ok * (err_sorted > thr).to(torch.int64), 0)
+    good = n_bad <= torch.floor(frac * n_ok.double()).to(torch.int64)
+    idx = torch.nonzero(good)
+    return int(idx.max().item()) if idx.numel() else -1
+
+
 def calibrate(sur: Surrogate, val: Dataset, tol: float = 1e-4, margin: float = 2.0, mu_max: float = 2.0,
               b_max: float = 10.0, caustic_min: float = -1.0, A_max: float = 10.0, rho_min: float = 5e-4,
-              A_small: float = 2.0) -> Gate:
+              A_small: float = 2.0, exceed_frac: float = EXCEED_FRAC) -> Gate:
     """Gate thresholds.  The physical ones are fixed:
-      - |b| <= 10 (the second-order estimate within 1e-3, so its neglected
-        higher orders are ~1e-6);
+      - |b| <= 10 (the second-order estimate within 1e-3), together with the
+        limb roughness of the feature status (ICRS_ST_ROUGH: structure on
+        the source's scale, where higher orders are not negligible);
       - |mu| <= 2 (the network corrects the estimate only slightly);
-      - min |det J| >= 0.1 over the nine point-source solves;
+      - min |det J| >= 0.1 over the 33 point-source solves;
       - A_ps <= 10, and A_ps <= 2 when rho < 5e-4 (small sources away from
         the far field, and all sources at high magnification, are where
         ICRS at the headline grid itself still moves by 1e-4 between grid
         refinements, so no surrogate can track it to 1e-4).
-    sigma_max is the largest value at which every accepted validation epoch
-    stays within tol / margin of ICRS."""
+    sigma_max is the largest value at which the accepted validation epochs
+    stay within tol / margin of ICRS, up to exceed_frac of them."""
     import torch
     pred = sur.predict(val.feat)
     mu, s = pred[:, 0].double(), pred[:, 1].double()
@@ -166,39 +189,36 @@ def calibrate(sur: Surrogate, val: Dataset, tol: float = 1e-4, margin: float = 2
     base = ((val.st == 0) & (val.feat[:, 6] >= caustic_min) & (mu.abs() <= mu_max) & (b.abs() <= b_max)
             & (val.A_ps <= torch.where(val.feat[:, 4] >= float(np.log10(rho_min)) + 3.0, A_max, A_small)))
     order = torch.argsort(sig)
-    e_sorted = torch.where(base[order], err[order], torch.zeros_like(err))
-    good = torch.cummax(e_sorted, 0).values <= tol / margin
-    smax = float(sig[order][int(torch.nonzero(good).max().item())].item()) if bool(good[0]) else 0.0
+    last = _loosest_prefix(base[order], err[order], tol / margin, exceed_frac)
+    smax = float(sig[order][last].item()) if last >= 0 else 0.0
     return Gate(smax, mu_max, b_max, caustic_min, A_max, rho_min, A_small)
 
 
-def calibrate_point_source(val: Dataset, tol: float = 1e-4, margin: float = 2.0, use_estimate: bool = False):
+def calibrate_point_source(val: Dataset, tol: float = 1e-4, margin: float = 2.0, use_estimate: bool = False,
+                           exceed_frac: float = EXCEED_FRAC):
     """The method without the network: A = A_ps (use_estimate: A = A_ps
     exp(1e-4 b), the second-order estimate) where the solves are clean and the
     caustic feature is at least c; returns the smallest c whose accepted
-    validation epochs stay within tol / margin."""
+    validation epochs stay within tol / margin (up to exceed_frac of them
+    beyond it)."""
     import torch
     Aest = val.A_ps * torch.exp(val.feat[:, 7].double() / icrs.TARGET_SCALE) if use_estimate else val.A_ps
     err = (Aest / val.A - 1.0).abs()
     c = val.feat[:, 6].double()
     ok = val.st == 0
     order = torch.argsort(c, descending=True)
-    e = torch.where(ok[order], err[order], torch.zeros_like(err))
-    good = torch.cummax(e, 0).values <= tol / margin
-    if not bool(good[0]):
-        return 2.0
-    last = int(torch.nonzero(good).max().item())
-    return float(c[order][last].item())
+    last = _loosest_prefix(ok[order], err[order], tol / margin, exceed_frac)
+    return float(c[order][last].item()) if last >= 0 else 2.0
 
 
 def calibrate_estimate(val: Dataset, tol: float = 1e-4, margin: float = 2.0,
                        caustic_grid=(-6.0, -3.0, -2.0, -1.5, -1.0, -0.5, 0.0),
                        b_grid=(1.0, 3.0, 10.0, 30.0, 100.0, 300.0), A_max: float = 10.0, rho_min: float = 5e-4,
-                       A_small: float = 2.0):
+                       A_small: float = 2.0, exceed_frac: float = EXCEED_FRAC):
     """The second-order estimate without the network, A = A_ps exp(1e-4 b),
     with the same A_ps <= A_max cut: the (caustic_min, b_max) that accepts
-    the most validation epochs while all of them stay within tol / margin.
-    Returns (caustic_min, b_max)."""
+    the most validation epochs while they stay within tol / margin (up to
+    exceed_frac of them beyond it).  Returns (caustic_min, b_max)."""
     import torch
     b = val.feat[:, 7].double()
     err = (val.A_ps * torch.exp(b / icrs.TARGET_SCALE) / val.A - 1.0).abs()
@@ -208,6 +228,7 @@ def calibrate_estimate(val: Dataset, tol: float = 1e-4, margin: float = 2.0,
             sel = ((val.st == 0) & (val.feat[:, 6] >= c) & (b.abs() <= bm)
                    & (val.A_ps <= torch.where(val.feat[:, 4] >= float(np.log10(rho_min)) + 3.0, A_max, A_small)))
             n = int(sel.sum().item())
-            if n > best_n and (n == 0 or float(err[sel].max()) <= tol / margin):
+            n_bad = int((err[sel] > tol / margin).sum().item())
+            if n > best_n and n_bad <= int(np.floor(exceed_frac * n)):
                 best, best_n = (float(c), float(bm)), n
     return best

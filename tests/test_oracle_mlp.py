@@ -114,3 +114,44 @@ def test_second_order_estimate_single_lens(oracle_mod):
         est = Aps[0] * np.exp(f[0, 7] * 1e-4)
         assert abs(est / exact - 1.0) < 3.0 * (rho / u) ** 4, (u_over_rho, est, exact, Aps[0])
         assert abs(Aps[0] / exact - 1.0) > 10 * abs(est / exact - 1.0)
+
+
+def test_limb_roughness_single_lens_closed_form(oracle_mod):
+    """Single lens (q = 1e-9, s = 50; the source centre at (0, u)): H of the
+    features equals the angular harmonics of order >= 3 of the closed-form
+    point-lens magnification A(x) = (x^2 + 2) / (x sqrt(x^2 + 4)) around the
+    limb, projected on a fine grid of 4096 angles: orders +-3..+-15, and
+    C_16 + C_-16 for the Nyquist bin.  Bin m of the 32-point transform holds
+    sum_j C_{m + 32 j}, so the two differ by at most sum_{|n| >= 17} |C_n| / A_c
+    (aliasing), plus 27 times the largest deviation of the oracle's
+    point-source magnification from the closed form at the 32 limb points
+    (each bin averages those deviations).  ST_ROUGH is set exactly where
+    H > 1e-3."""
+    from paper_2510_02639_gb300 import inputs as I
+    rho, q, s = 0.01, 1e-9, 50.0
+    a1 = -q * s / (1.0 + q)
+    eps1 = 1.0 / (1.0 + q)
+
+    def A_pl(z):
+        x = np.abs(z - a1) / np.sqrt(eps1)
+        return (x * x + 2.0) / (x * np.sqrt(x * x + 4.0))
+
+    phi = np.linspace(0.0, 2.0 * np.pi, 4096, endpoint=False)
+    seen = set()
+    for u_over_rho in (2.5, 5.0, 12.0, 40.0):
+        u = u_over_rho * rho
+        p = I.binary(q=q, s=s, rho=rho, u1=0.5, u0=u, t0=0.0, tE=1.0, alpha=0.0)
+        f, Aps, st, H = M.features(p, [0.0], I.grid(), return_roughness=True)
+        wc = 1j * u
+        Ak = A_pl(wc + rho * np.exp(1j * phi))
+        C = {m: np.mean(Ak * np.exp(-1j * m * phi)) for m in range(-127, 128)}
+        H_cf = (sum(abs(C[m]) + abs(C[-m]) for m in range(3, 16)) + abs(C[16] + C[-16])) / A_pl(wc)
+        alias = sum(abs(C[m]) for m in C if abs(m) >= 17) / A_pl(wc)
+        zk = wc + rho * np.exp(1j * np.pi * np.arange(32) / 16.0)
+        dev = np.max(np.abs(oracle_mod.point_source(p, I.grid(), zk)[0] - A_pl(zk))) / A_pl(wc)
+        assert dev < 1e-7  # the companion's constant deflection shifts the source by ~q / s
+        assert abs(H[0] - H_cf) <= alias + 27.0 * dev + 1e-12, (u_over_rho, H[0], H_cf, alias, dev)
+        rough = bool(st[0] & M.ST_ROUGH)
+        assert rough == (H_cf > M.ROUGH_MAX), (u_over_rho, H_cf)
+        seen.add(rough)
+    assert seen == {True, False}
