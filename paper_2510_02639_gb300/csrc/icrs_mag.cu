@@ -35,8 +35,15 @@
 
 namespace icrs {
 
-constexpr int NT = 512;          // threads per block (one block per SM)
-constexpr int NW = NT / 32;      // warps per block
+// Threads per block (one block per SM) of an instantiation.  The binary
+// forward kernel runs 768 threads: its root phases fit in 80 registers with
+// small spills, and the ray stage, bound by instruction issue and
+// dependency latency, gains from the 24 warps per SM (+19% over 512 at the
+// 1024 x 2048 grid).  The derivative and triple instantiations keep 512
+// threads (128 registers): at 80 their FP64 phases spill kilobytes.
+__host__ __device__ constexpr int mag_threads(int nl, bool der) { return (nl == 2 && !der) ? 768 : 512; }
+constexpr int NW_MAX = 24;                      // warps per block, largest instantiation
+constexpr int NW_DER = mag_threads(2, true) / 32;  // warps per block, derivative mode
 constexpr int QMAX = 2048;       // work queue
 constexpr int PMAX_MIN = 512;    // FP64-polished image-limb points per epoch (at least)
 constexpr int MAXT = 32;         // theta runs (<= n_bins_theta / 2)
@@ -50,9 +57,10 @@ constexpr float TINY_EXTENT = 3e-4f;  // images smaller than this x rho skip FP6
 constexpr float EPS32 = 5.9604645e-8f;  // 2^-24
 
 // Rays per row segment.  Forward: 508, so that a segment and its 4-ray halo
-// fill exactly 8 iterations of 32 lanes x 2 rays; the row buffers then leave
-// room for an FP64 point table that holds every image-limb point at n_theta
-// = 2048.  Derivative mode: 256 (its per-ray seeds take the same room again).
+// fill exactly 8 iterations of 32 lanes x 2 rays, with row buffers small
+// enough to leave room for an FP64 point table of 1024 (768 threads) to 2500
+// entries at n_theta = 2048.  Derivative mode: 256 (its per-ray seeds take the
+// same room again).
 __host__ __device__ __forceinline__ int row_segment(int n_theta, bool der) {
   const int segmax = der ? 256 : 508;
   return n_theta < segmax ? n_theta : segmax;
@@ -118,7 +126,7 @@ struct Shared {
   double dr64, dth64;
   float dr32, dth32;
   int nanch;
-  double red[NW];
+  double red[NW_MAX];
 };
 
 // Derivative-mode state (binary lens), in the dynamic shared memory of that
@@ -132,8 +140,8 @@ struct DerShared {
   double depsq[2];          // d eps_j / d q
   DualD cx[MAXCELL_D * 4];  // cell extremes with tangents
   BoxT<DualD> box[MAXBOX_D];  // sectors with tangents
-  double wder[NW][12];      // per-warp sums of the row derivatives
-  double bdist[NW][6][5];   // FP64 stencil distances of up to 6 boundary points per warp
+  double wder[NW_DER][12];      // per-warp sums of the row derivatives
+  double bdist[NW_DER][6][5];   // FP64 stencil distances of up to 6 boundary points per warp
   float2 acs[MAXANCH];      // cos, sin of each anchor angle
 };
 
@@ -455,12 +463,15 @@ struct DerOut {
 };
 
 template <int NL, bool DER>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(mag_threads(NL, DER), 1)
 mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ T_, int E,
            icrs_grid g, int tiles_per_block, double* __restrict__ A_out, uint32_t* __restrict__ st_out,
            double* __restrict__ diag_sect, int32_t* __restrict__ diag_cnt, float* __restrict__ diag_pts, int PMAX,
            int has_plo, DerOut dout, const int32_t* __restrict__ items, int n_items, int defer) {
   constexpr int N = NL * NL + 1;
+  constexpr int NT = mag_threads(NL, DER);
+  constexpr int NW = NT / 32;
+  static_assert(NW <= NW_MAX && (!DER || NW == NW_DER), "per-warp tables are sized for these block sizes");
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Shared sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1947,6 +1958,7 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += sizeof(short) * ((NP + 7) & ~(size_t)7);
   b += 3 * ((NP + 15) & ~(size_t)15);
   b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
+  const int NW = mag_threads(NL, der) / 32;
   b += sizeof(int) * NW * ((!der && NL == 2 && defer) ? 256 : 64);  // per-warp boundary queues
   const int seg = row_segment(g.n_theta, der);
   if (der) b += sizeof(DerShared) + sizeof(float) * NW * (seg + 4);  // state and ray seeds
@@ -2014,6 +2026,7 @@ static int launch_inst(const icrs_params* p, int S, const double* t, int E, cons
   if (cudaFuncSetAttribute(mag_kernel<NL, DER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return ICRS_ECUDA;
   int per_sm = 0;
+  constexpr int NT = mag_threads(NL, DER);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mag_kernel<NL, DER>, NT, smem) != cudaSuccess) return ICRS_ECUDA;
   if (per_sm < 1) return ICRS_EUNSUPPORTED;
   long long tiles = items ? (long long)n_items : (long long)S * E;
