@@ -23,6 +23,7 @@
 //     the decisions equal those of an FP64 evaluation of the same method;
 //   * rays are mapped in FP32 in a difference form about FP64 anchors placed
 //     on the sector, so the FP32 error stays relative to the source size.
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -1576,7 +1577,11 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           // RPL independent rays per lane and iteration (instruction-level
           // parallelism for the dependent FP32 chains of the lens map)
           constexpr int RPL = 2;
-          for (int m0 = lane; m0 < cnt; m0 += 32 * RPL) {
+          // one fill iteration, RPL rays per lane.  INNER: all 32 x RPL rays
+          // of the warp lie inside the segment and inside [0, N_theta), so
+          // none needs wrapping or the beyond-the-grid marker
+          auto fill = [&](const int m0, auto inner) {
+            constexpr bool INNER = decltype(inner)::value;
             float a_[RPL];
             bool u_[RPL], x_[RPL];
             int lw_[RPL];
@@ -1584,8 +1589,13 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             for (int r = 0; r < RPL; ++r) {
               const int m = m0 + 32 * r;
               const int l = lo + m;
-              x_[r] = m >= cnt || (!B.periodic && (l < 0 || l >= NTH));
-              lw_[r] = x_[r] ? 0 : wrapl(l);
+              if constexpr (INNER) {
+                x_[r] = false;
+                lw_[r] = l;
+              } else {
+                x_[r] = m >= cnt || (!B.periodic && (l < 0 || l >= NTH));
+                lw_[r] = x_[r] ? 0 : wrapl(l);
+              }
             }
 #pragma unroll
             for (int r = 0; r < RPL; ++r) u_[r] = ray_d2(lw_[r], &a_[r]);
@@ -1600,8 +1610,16 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                 v = d64 < sh.rho ? -q : q;
               }
               if (v == 0.f && a_[r] < rho32 * rho32) v = -0.0f;
-              if (m < cnt) buf[m] = x_[r] ? __int_as_float(0x7f800000) : v;
+              if constexpr (INNER) buf[m] = v;
+              else if (m < cnt) buf[m] = x_[r] ? __int_as_float(0x7f800000) : v;
             }
+          };
+          for (int m0 = lane; m0 < cnt; m0 += 32 * RPL) {
+            const int mb = m0 - lane;  // first ray of the warp's iteration
+            if (mb + 32 * RPL <= cnt && lo + mb >= 0 && lo + mb + 32 * RPL <= NTH)
+              fill(m0, std::true_type{});
+            else
+              fill(m0, std::false_type{});
           }
           float* ab = abuf + warp * (seg + 4);
           if (DER)
