@@ -338,6 +338,8 @@ def main():
     ap.add_argument("--sur-train-sets", type=int, default=200, help="surrogate training sets x 2000 epochs (0: skip)")
     ap.add_argument("--sur-query-sets", type=int, default=250, help="surrogate scoring sets x 2000 epochs")
     ap.add_argument("--sur-epochs", type=int, default=30)
+    ap.add_argument("--clocks-csv", default="", help="where the nvidia-smi samples of the timed steps go "
+                                                     "({rank} is replaced); default /tmp/clocks_rank{rank}.csv")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -382,8 +384,7 @@ def main():
         step()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clk = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/clocks_rank{rank}.csv")
+    clk = ClockSampler(args.clocks_csv.format(rank=rank) if args.clocks_csv else f"/tmp/clocks_rank{rank}.csv")
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
