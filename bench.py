@@ -86,6 +86,25 @@ def workload(name, rank=0):
     return params, t, desc
 
 
+def reduce_max(x: float, world: int, device) -> float:
+    """Maximum of a per-rank time over the ranks of the job (x itself when
+    the job has one rank): each replica's throughput counts against the
+    slowest rank's clock."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+def job_rate(units_per_rank: int, world: int, steps: int, t_max_s: float) -> float:
+    """Whole-job throughput of weak-scaling replicas: every rank processes
+    units_per_rank per step, timed by the slowest rank."""
+    return units_per_rank * world * steps / t_max_s
+
+
 class ClockSampler:
     def __init__(self, path):
         self.path = path
@@ -402,12 +421,8 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_local = float(np.sum(step_ms)) / 1e3
-    t_max = t_local
-    if world > 1:
-        x = torch.tensor([t_local], device=dev)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        t_max = float(x.item())
-    value = S * E * world * args.steps / t_max
+    t_max = reduce_max(t_local, world, dev)
+    value = job_rate(S * E, world, args.steps, t_max)
 
     # rays evaluated (sector count in status bits 8..15)
     stc = st.cpu().numpy().astype(np.int64)
@@ -435,8 +450,8 @@ def main():
         h_A.copy_(A, non_blocking=True)
         h_st.copy_(st, non_blocking=True)
         torch.cuda.synchronize()
-    w = (time.perf_counter() - w0) / n_e2e
-    e2e = {"value": S * E * world / w, "unit": "magnifications/s",
+    w = reduce_max((time.perf_counter() - w0) / n_e2e, world, dev)
+    e2e = {"value": job_rate(S * E, world, 1, w), "unit": "magnifications/s",
            "h2d_bytes_per_step": int(h_params.numel() + h_t.numel() * 8),
            "d2h_bytes_per_step": int(h_A.numel() * 8 + h_st.numel() * 4)}
 
@@ -447,7 +462,8 @@ def main():
     gridf = icrs.grid_from_dict(gf, n_lens)
     msf = timed_steps(lambda: icrs.magnification(pd, tt, gridf, out=A, status=st, stream=stream), args.steps,
                       args.warmup, flush, stream)
-    fixed = {"grid": grid_desc(gf), "value": S * E * world * args.steps / (float(np.sum(msf)) / 1e3),
+    fixed = {"grid": grid_desc(gf),
+             "value": job_rate(S * E, world, args.steps, reduce_max(float(np.sum(msf)) / 1e3, world, dev)),
              "unit": "magnifications/s", "ms_per_step": float(np.mean(msf)),
              "accuracy": accuracy(icrs, I, gf, dev) if args.workload == "batch" else None}
 
