@@ -140,6 +140,24 @@ def test_full_batch_sampled(G, oracle_mod):
         assert abs(A[s, e] / Ao[0, 0] - 1.0) <= TOL, (s, e, A[s, e], Ao[0, 0])
 
 
+def test_headline_grid_full_batch_sampled(G, oracle_mod):
+    """The benchmark's headline launch: the 64 x 10,000 batch in one call at
+    n_r = 1024, n_theta = 2048 (the 768-thread binary kernel, 508-ray row
+    segments, warm starts along each light curve).  The oracle recomputes 24
+    sampled epochs on the same grid: the highest-magnification epoch of 8
+    sets and 16 random ones."""
+    params, t = I.binary_batch()
+    g = I.grid(n_r=1024, n_theta=2048)
+    A, st = run_gpu(G, params, t, g)
+    assert np.all(np.isfinite(A))
+    rng = np.random.default_rng(7)
+    picks = [(s, int(np.argmax(A[s]))) for s in range(0, len(params), 8)]
+    picks += [(int(rng.integers(len(params))), int(rng.integers(t.shape[1]))) for _ in range(16)]
+    for s, e in picks:
+        Ao, _ = oracle_mod.magnification([params[s]], [t[s, e]], g)
+        assert abs(A[s, e] / Ao[0, 0] - 1.0) <= TOL, (s, e, A[s, e], Ao[0, 0])
+
+
 def test_empty_and_invalid(G):
     import torch
     pd = G.params_to_device([I.binary()])
