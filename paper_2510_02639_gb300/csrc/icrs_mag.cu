@@ -36,15 +36,18 @@
 
 namespace icrs {
 
-// Threads per block (one block per SM) of an instantiation.  The binary
-// forward kernel runs 768 threads: its root phases fit in 80 registers with
-// small spills, and the ray stage, bound by instruction issue and
-// dependency latency, gains from the 24 warps per SM (+19% over 512 at the
-// 1024 x 2048 grid).  The derivative and triple instantiations keep 512
-// threads (128 registers): at 80 their FP64 phases spill kilobytes.
-__host__ __device__ constexpr int mag_threads(int nl, bool der) { return (nl == 2 && !der) ? 768 : 512; }
-constexpr int NW_MAX = 24;                      // warps per block, largest instantiation
-constexpr int NW_DER = mag_threads(2, true) / 32;  // warps per block, derivative mode
+// Threads per block (one block per SM).  The binary forward kernel prefers
+// 768 threads: its root phases fit in 80 registers with small spills, and
+// the ray stage, bound by instruction issue and dependency latency, gains
+// from the 24 warps per SM (+19% over 512 at the 1024 x 2048 grid).  Where
+// the wider layout's per-warp buffers do not fit in shared memory (n_theta
+// = 8192 at N_limb = 500), it falls back to a 512-thread instantiation.  The
+// derivative and triple instantiations keep 512 threads (128 registers): at
+// 80 their FP64 phases spill kilobytes.
+constexpr int NT_WIDE = 768, NT_BASE = 512;
+__host__ __device__ constexpr int mag_threads(int nl, bool der) { return (nl == 2 && !der) ? NT_WIDE : NT_BASE; }
+constexpr int NW_MAX = NT_WIDE / 32;  // warps per block, largest instantiation
+constexpr int NW_DER = NT_BASE / 32;  // warps per block, derivative mode
 constexpr int QMAX = 2048;       // work queue
 constexpr int PMAX_MIN = 512;    // FP64-polished image-limb points per epoch (at least)
 constexpr int MAXT = 32;         // theta runs (<= n_bins_theta / 2)
@@ -463,16 +466,16 @@ struct DerOut {
   double* chi2;        // [S] accumulated, or NULL
 };
 
-template <int NL, bool DER>
-__global__ void __launch_bounds__(mag_threads(NL, DER), 1)
+template <int NL, bool DER, int NTB>
+__global__ void __launch_bounds__(NTB, 1)
 mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ T_, int E,
            icrs_grid g, int tiles_per_block, double* __restrict__ A_out, uint32_t* __restrict__ st_out,
            double* __restrict__ diag_sect, int32_t* __restrict__ diag_cnt, float* __restrict__ diag_pts, int PMAX,
            int has_plo, DerOut dout, const int32_t* __restrict__ items, int n_items, int defer) {
   constexpr int N = NL * NL + 1;
-  constexpr int NT = mag_threads(NL, DER);
+  constexpr int NT = NTB;
   constexpr int NW = NT / 32;
-  static_assert(NW <= NW_MAX && (!DER || NW == NW_DER), "per-warp tables are sized for these block sizes");
+  static_assert(NT % 32 == 0 && NW <= NW_MAX && (!DER || NW == NW_DER), "per-warp tables are sized for these block sizes");
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ Shared sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1968,7 +1971,7 @@ __global__ void point_source_kernel(const icrs_params* __restrict__ P, int S, co
 }
 
 // ---------------------------------------------------------------- host side
-static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, bool der, int defer) {
+static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, bool der, int defer, int nt) {
   const int N = NL * NL + 1;
   const size_t NP = (size_t)g.n_limb * N;
   size_t b = has_plo ? sizeof(cf) * NP : 0;
@@ -1976,7 +1979,7 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += sizeof(short) * ((NP + 7) & ~(size_t)7);
   b += 3 * ((NP + 15) & ~(size_t)15);
   b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
-  const int NW = mag_threads(NL, der) / 32;
+  const int NW = nt / 32;
   b += sizeof(int) * NW * ((!der && NL == 2 && defer) ? 256 : 64);  // per-warp boundary queues
   const int seg = row_segment(g.n_theta, der);
   if (der) b += sizeof(DerShared) + sizeof(float) * NW * (seg + 4);  // state and ray seeds
@@ -2012,9 +2015,38 @@ static int first_n_lens(const icrs_params* p, cudaStream_t st, int* nl) {
   return ICRS_OK;
 }
 
-// Launch of one instantiation: shared-memory sizing (the FP64 point table
-// takes what is left, up to one entry per image-limb slot), occupancy, contiguous chunks of
-// epochs per block (warm starts along the light curve).
+// Launch of one instantiation at NTB threads per block, with its shared
+// memory, point-table size and flags already chosen: occupancy, contiguous
+// chunks of epochs per block (warm starts along the light curve).
+template <int NL, bool DER, int NTB>
+static int launch_nt(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, double* A,
+                     uint32_t* status, double* dsect, int32_t* dcnt, float* dpts, const DerOut& dout,
+                     cudaStream_t st, const int32_t* items, int n_items, int nsm, size_t smem, int pmax,
+                     int has_plo, int defer) {
+  if (cudaFuncSetAttribute(mag_kernel<NL, DER, NTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return ICRS_ECUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mag_kernel<NL, DER, NTB>, NTB, smem) != cudaSuccess)
+    return ICRS_ECUDA;
+  if (per_sm < 1) return ICRS_EUNSUPPORTED;
+  long long tiles = items ? (long long)n_items : (long long)S * E;
+  long long slots = (long long)nsm * per_sm;
+  long long per_block = (tiles + slots - 1) / slots;
+  if (per_block < 1) per_block = 1;
+  long long blocks = (tiles + per_block - 1) / per_block;
+  mag_kernel<NL, DER, NTB><<<(unsigned)blocks, NTB, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect,
+                                                                 dcnt, dpts, pmax, has_plo, dout, items, n_items,
+                                                                 defer);
+  return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
+}
+
+// Shared-memory sizing of one (NL, DER) launch: the block size (the
+// preferred one, else 512 threads when the preferred layout does not fit),
+// the deferred boundary queue (binary forward) if it fits; then, forward,
+// the FP64 point table grows (up to one entry per image-limb slot) before
+// the lo parts of image positions are added; derivative mode takes the lo
+// parts first (fewer FP64 polishes).
 template <int NL, bool DER>
 static int launch_inst(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, double* A,
                        uint32_t* status, double* dsect, int32_t* dcnt, float* dpts, const DerOut& dout,
@@ -2024,37 +2056,32 @@ static int launch_inst(const icrs_params* p, int S, const double* t, int E, cons
   int optin = 0, nsm = 0;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return ICRS_ECUDA;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ICRS_ECUDA;
-  // shared memory: the deferred boundary queue (binary forward) if it fits;
-  // then, forward, the FP64 point table grows (up to one entry per
-  // image-limb slot) before the lo parts of image positions are added;
-  // derivative mode takes the lo parts first (fewer FP64 polishes)
+  int nt = mag_threads(NL, DER);
   auto fits = [&](int pm, int plo, int df) {
-    return mag_smem_bytes(NL, *g, pm, plo, DER, df) + sizeof(Shared) <= (size_t)optin;
+    return mag_smem_bytes(NL, *g, pm, plo, DER, df, nt) + sizeof(Shared) <= (size_t)optin;
   };
   int pmax = PMAX_MIN;
   int defer = (NL == 2 && !DER) ? 1 : 0;
   if (!fits(pmax, 0, defer)) defer = 0;
+  if (!fits(pmax, 0, defer) && nt != NT_BASE) {
+    nt = NT_BASE;
+    defer = (NL == 2 && !DER) ? 1 : 0;
+    if (!fits(pmax, 0, defer)) defer = 0;
+  }
   if (!fits(pmax, 0, defer)) return ICRS_EUNSUPPORTED;
   int has_plo = (DER && fits(pmax, 1, defer)) ? 1 : 0;
   const int np_all = g->n_limb * (NL * NL + 1);
   while (pmax < np_all && fits(pmax * 2 < np_all ? pmax * 2 : np_all, has_plo, defer))
     pmax = pmax * 2 < np_all ? pmax * 2 : np_all;
   if (!DER) has_plo = fits(pmax, 1, defer) ? 1 : 0;
-  size_t smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER, defer);
-  if (cudaFuncSetAttribute(mag_kernel<NL, DER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return ICRS_ECUDA;
-  int per_sm = 0;
-  constexpr int NT = mag_threads(NL, DER);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mag_kernel<NL, DER>, NT, smem) != cudaSuccess) return ICRS_ECUDA;
-  if (per_sm < 1) return ICRS_EUNSUPPORTED;
-  long long tiles = items ? (long long)n_items : (long long)S * E;
-  long long slots = (long long)nsm * per_sm;
-  long long per_block = (tiles + slots - 1) / slots;
-  if (per_block < 1) per_block = 1;
-  long long blocks = (tiles + per_block - 1) / per_block;
-  mag_kernel<NL, DER><<<(unsigned)blocks, NT, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect, dcnt,
-                                                          dpts, pmax, has_plo, dout, items, n_items, defer);
-  return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
+  const size_t smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER, defer, nt);
+  if constexpr (mag_threads(NL, DER) != NT_BASE) {
+    if (nt == mag_threads(NL, DER))
+      return launch_nt<NL, DER, mag_threads(NL, DER)>(p, S, t, E, g, A, status, dsect, dcnt, dpts, dout, st, items,
+                                                      n_items, nsm, smem, pmax, has_plo, defer);
+  }
+  return launch_nt<NL, DER, NT_BASE>(p, S, t, E, g, A, status, dsect, dcnt, dpts, dout, st, items, n_items, nsm,
+                                     smem, pmax, has_plo, defer);
 }
 
 static int launch_mag(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g,

@@ -158,6 +158,18 @@ def test_headline_grid_full_batch_sampled(G, oracle_mod):
         assert abs(A[s, e] / Ao[0, 0] - 1.0) <= TOL, (s, e, A[s, e], Ao[0, 0])
 
 
+def test_wide_theta_grid(G, oracle_mod):
+    """n_theta = 8192 at N_limb = 500 (the paper's finest angular resolution
+    is 8000): the 768-thread binary layout does not fit in shared memory
+    there, so the launch takes the 512-thread instantiation.  8 epochs of the
+    caustic-crossing curve against the oracle on the same grid."""
+    params, t = I.caustic_crossing_binary(n_epochs=8)
+    g = I.grid(n_r=64, n_theta=8192)
+    A, st = run_gpu(G, params, t, g)
+    Ao, so = oracle_mod.magnification(params, t, g)
+    assert_parity(A, Ao, what="n_theta 8192")
+
+
 def test_empty_and_invalid(G):
     import torch
     pd = G.params_to_device([I.binary()])
