@@ -23,9 +23,9 @@ _lib = None
 
 # Parameter vector layout used by the oracle's C entry points.
 PARAM_FIELDS = ("t0", "tE", "u0", "alpha", "rho", "u1", "n_lens",
-                "s", "q", "q2", "q3", "s2", "s3", "psi")
+                "s", "q", "q2", "q3", "s2", "s3", "psi", "u2")
 GRID_FIELDS = ("n_r", "n_theta", "n_limb", "n_bins_r", "n_bins_theta",
-               "max_iter", "uniform", "delta_c", "margin", "img_tol")
+               "max_iter", "uniform", "delta_c", "margin", "img_tol", "ld_split")
 
 
 def build(force: bool = False) -> str:
@@ -76,7 +76,7 @@ def _d(a):
 
 
 def param_vector(p: dict) -> np.ndarray:
-    """Flatten a parameter dict into the oracle's 14-slot layout."""
+    """Flatten a parameter dict into the oracle's 15-slot layout."""
     out = np.zeros(len(PARAM_FIELDS))
     for i, k in enumerate(PARAM_FIELDS):
         out[i] = float(p.get(k, 0.0))
@@ -84,7 +84,7 @@ def param_vector(p: dict) -> np.ndarray:
 
 
 def grid_vector(g: dict) -> np.ndarray:
-    return np.array([float(g[k]) for k in GRID_FIELDS])
+    return np.array([float(g.get(k, 0)) for k in GRID_FIELDS])
 
 
 def lens(p: dict):

@@ -97,12 +97,14 @@ typedef Cx<double> C;
 
 // ----------------------------------------------------------------------------
 // Inputs (flat arrays so the Python side needs no shared struct definition).
-// params[14] = t0, tE, u0, alpha, rho, u1, n_lens, s, q, q2, q3, s2, s3, psi
-// grid[10]   = n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter,
-//              uniform, delta_c, margin, img_tol
+// params[15] = t0, tE, u0, alpha, rho, u1, n_lens, s, q, q2, q3, s2, s3, psi,
+//              u2
+// grid[11]   = n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter,
+//              uniform, delta_c, margin, img_tol, ld_split
 // ----------------------------------------------------------------------------
+const int NPRM = 15;  // slots of one parameter set
 struct Grid {
-  int n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter, uniform;
+  int n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter, uniform, ld_split;
   double delta_c, margin, img_tol;
 };
 Grid grid_from(const double* g) {
@@ -110,6 +112,7 @@ Grid grid_from(const double* g) {
   G.n_r = (int)g[0]; G.n_theta = (int)g[1]; G.n_limb = (int)g[2];
   G.n_bins_r = (int)g[3]; G.n_bins_theta = (int)g[4]; G.max_iter = (int)g[5];
   G.uniform = (int)g[6]; G.delta_c = g[7]; G.margin = g[8]; G.img_tol = g[9];
+  G.ld_split = (int)g[10];
   return G;
 }
 
@@ -418,13 +421,13 @@ double point_source(const Lens<double>& L, C w, const Grid& G, uint32_t* st, C* 
 // Parameters -> trajectory (Sec. 3.5 parameter list; Fig. 3 for the angle).
 // READING: w_c = tau (cos a, sin a) + u0 (-sin a, cos a), tau = (t - t0)/tE.
 // ----------------------------------------------------------------------------
-template <class T> struct Par { T t0, tE, u0, alpha, s, q, rho, u1; };
+template <class T> struct Par { T t0, tE, u0, alpha, s, q, rho, u1; double u2; };
 
 template <class T> Par<T> par_from(const double* p, bool seed);
 template <> Par<double> par_from<double>(const double* p, bool) {
   Par<double> P;
   P.t0 = p[0]; P.tE = p[1]; P.u0 = p[2]; P.alpha = p[3]; P.rho = p[4]; P.u1 = p[5];
-  P.s = p[7]; P.q = p[8];
+  P.s = p[7]; P.q = p[8]; P.u2 = p[14];
   return P;
 }
 template <> Par<Dual> par_from<Dual>(const double* p, bool) {
@@ -437,6 +440,7 @@ template <> Par<Dual> par_from<Dual>(const double* p, bool) {
   P.q = Dual(p[8]); P.q.d[5] = 1.0;
   P.rho = Dual(p[4]); P.rho.d[6] = 1.0;
   P.u1 = Dual(p[5]); P.u1.d[7] = 1.0;
+  P.u2 = p[14];
   return P;
 }
 
@@ -767,20 +771,38 @@ T fdelta(const T& delta, const Grid& G) {
   return (2.0 / 3.0) * delta + 0.5;
 }
 
-// Linear limb darkening I(rt) = I0 [1 - u1 (1 - sqrt(1 - rt^2))],
-// I0 = 3 / (pi (3 - u1))  (Appendix A.2); uniform: 1/pi.
+// Limb darkening (Appendix A.2 gives the linear law; the quadratic law adds
+// the next term in (1 - mu), mu = sqrt(1 - rt^2)):
+//   I(rt) = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2],
+//   I0 = 1 / (pi (1 - u1/3 - u2/6))   (= 3 / (pi (3 - u1)) for u2 = 0,
+// the normalisation of Appendix A.2: the total flux is 1); uniform: 1/pi.
 template <class T>
-T brightness(const T& rt2, const T& u1, const Grid& G) {
+T brightness(const T& rt2, const T& u1, double u2, const Grid& G) {
   if (G.uniform) return T(1.0 / PI);
-  T I0 = 3.0 / (PI * (3.0 - u1));
+  T I0 = 1.0 / (PI * (1.0 - u1 / 3.0 - u2 / 6.0));
   T one = T(1.0);
   T x = one - rt2;
   if (val(x) < 0) x = T(0.0);
-  return I0 * (one - u1 * (one - sqrt(x)));
+  T om = one - sqrt(x);
+  return I0 * (one - u1 * om - u2 * (om * om));
+}
+
+// The same law at the limb (mu = 0): the part of I that jumps to zero across
+// the source edge.
+template <class T>
+T brightness_limb(const T& u1, double u2, const Grid& G) {
+  if (G.uniform) return T(1.0 / PI);
+  T I0 = 1.0 / (PI * (1.0 - u1 / 3.0 - u2 / 6.0));
+  return I0 * (1.0 - u1 - u2);
 }
 
 // Integral over one sector: sum_i A_i dr with
 //   A_i = r_i dtheta sum_l I_l chi_l W_l   (Appendix A.2 per-point rule).
+// Split-profile rule (G.ld_split = 1; a variant, not in the paper): the part
+// of I that is constant across the edge, I_limb, takes the uniform-source
+// weight W_U (f_U(delta) = delta + 1/2, exact for a step) and the rest,
+// which vanishes at the edge like sqrt(distance), the weight W of f(delta):
+//   I_l W_l  ->  I_limb W_U,l + (I_l - I_limb) W_l.
 // READING (per-point form for both profiles): W = 1 if both neighbours are
 // inside; f(delta_L) / f(delta_R) if the left / right neighbour is outside
 // with delta_L = (theta_l - theta_cross)/dtheta, delta_R = (theta_cross -
@@ -790,7 +812,7 @@ T brightness(const T& rt2, const T& u1, const Grid& G) {
 // linear fit (flag EDGE).
 template <class T>
 T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& rho,
-                  const T& u1, const Grid& G, uint32_t* st) {
+                  const T& u1, double u2, const Grid& G, uint32_t* st) {
   const int NR = G.n_r, NT = G.n_theta;
   T dr = (B.r_hi - B.r_lo) / (double)NR;
   T dth = B.width / (double)NT;
@@ -818,11 +840,12 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
       int lm = idx(l - 1), lp = idx(l + 1);
       bool Lin = lm >= 0 && chi[lm];
       bool Rin = lp >= 0 && chi[lp];
-      T W;
+      T W, WU;
       if (Lin && Rin) {
         W = T(1.0);
+        WU = T(1.0);
       } else {
-        T fL(0.0), fR(0.0);
+        T fL(0.0), fR(0.0), uL(0.0), uR(0.0);
         if (!Lin) {
           T dl;
           if (lm < 0) { dl = T(0.5); *st |= ST_EDGE; }
@@ -839,6 +862,7 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
             dl = -x;
           }
           fL = fdelta(dl, G);
+          uL = dl + 0.5;
         }
         if (!Rin) {
           T dd;
@@ -854,13 +878,22 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
             dd = crossing(xs, ys, npt, 0.0, 1.0, rho);
           }
           fR = fdelta(dd, G);
+          uR = dd + 0.5;
         }
-        if (Lin) W = fR;
-        else if (Rin) W = fL;
-        else { W = fL + fR - 1.0; if (val(W) < 0) W = T(0.0); }
+        if (Lin) { W = fR; WU = uR; }
+        else if (Rin) { W = fL; WU = uL; }
+        else {
+          W = fL + fR - 1.0; if (val(W) < 0) W = T(0.0);
+          WU = uL + uR - 1.0; if (val(WU) < 0) WU = T(0.0);
+        }
       }
-      T I = brightness(d[l] * d[l] / rho2, u1, G);
-      row = row + I * W;
+      T I = brightness(d[l] * d[l] / rho2, u1, u2, G);
+      if (G.ld_split && !G.uniform) {
+        T Il = brightness_limb(u1, u2, G);
+        row = row + Il * WU + (I - Il) * W;
+      } else {
+        row = row + I * W;
+      }
     }
     total = total + r * row;
   }
@@ -907,7 +940,7 @@ T magnification_epoch(const double* prm, double t, const Grid& G, uint32_t* st,
   if (boxes_out) *boxes_out = boxes;
   T sum(0.0);
   for (size_t b = 0; b < boxes.size(); ++b)
-    sum = sum + sector_integral(boxes[b], L, wc, P.rho, P.u1, G, st);
+    sum = sum + sector_integral(boxes[b], L, wc, P.rho, P.u1, P.u2, G, st);
   // A = sum_sectors A_sector / rho^2 (Appendix A.2; with I = 1/pi this is the
   // 1/(pi rho^2) normalisation of Appendix A.1).
   T A = sum / (P.rho * P.rho);
@@ -1022,14 +1055,14 @@ int orc_limb_points(const double* prm, double t, const double* grid, double* out
 }
 
 // Finite-source magnification for S parameter sets x E epochs.
-// prm[S][14], t[S][E], A[S][E], status[S][E] (optional).
+// prm[S][15], t[S][E], A[S][E], status[S][E] (optional).
 void orc_magnification(const double* prm, int S, const double* t, int E, const double* grid,
                        double* A, uint32_t* status) {
   Grid G = grid_from(grid);
   for (int s = 0; s < S; ++s)
     for (int e = 0; e < E; ++e) {
       uint32_t st = 0;
-      A[(size_t)s * E + e] = magnification_epoch<double>(prm + 14 * s, t[(size_t)s * E + e], G, &st, nullptr);
+      A[(size_t)s * E + e] = magnification_epoch<double>(prm + NPRM * s, t[(size_t)s * E + e], G, &st, nullptr);
       if (status) status[(size_t)s * E + e] = st;
     }
 }
@@ -1042,7 +1075,7 @@ void orc_magnification_fwd(const double* prm, int S, const double* t, int E, con
   for (int s = 0; s < S; ++s)
     for (int e = 0; e < E; ++e) {
       uint32_t st = 0;
-      Dual a = magnification_epoch<Dual>(prm + 14 * s, t[(size_t)s * E + e], G, &st, nullptr);
+      Dual a = magnification_epoch<Dual>(prm + NPRM * s, t[(size_t)s * E + e], G, &st, nullptr);
       size_t o = (size_t)s * E + e;
       A[o] = a.v;
       for (int i = 0; i < ND; ++i) dA[o * ND + i] = a.d[i];

@@ -95,6 +95,80 @@ def forward(theta, X, bf16=True):
     return Y, {"x": xs, "z": zs, "p": p, "bf16": bf16}
 
 
+U_BF16 = 2.0 ** -8   # unit roundoff of BF16 round-to-nearest (8 significant bits)
+U_FP32 = 2.0 ** -24
+
+
+def reference_forward(theta, X):
+    """The network with BF16-rounded weights and inputs and no other rounding
+    (every contraction and activation exact in FP64): the reference the
+    tensor-core kernels are compared with, element by element."""
+    p = unpack(theta)
+    xs = [bf16_round(X)]
+    zs = []
+    for l in range(4):
+        zs.append(xs[-1] @ bf16_round(p[f"W{l}"]).T + p[f"b{l}"])
+        xs.append(silu(zs[-1]))
+    Y = xs[-1] @ bf16_round(p["W4"]).T + p["b4"]
+    return Y, {"x": xs, "z": zs, "p": p, "bf16": False, "wr": True}
+
+
+def inference_bound(theta, X):
+    """Per-element first-order bound on |Y_kernel - Y_ref| for a kernel that,
+    beyond the reference's rounding of weights and inputs, rounds each hidden
+    activation X_l (l = 1..4) to BF16 (|r_l| <= 2^-8 |X_l| elementwise) and
+    accumulates every contraction of K terms in FP32 (error <= K 2^-24 of
+    the sum of the terms' magnitudes).  Linearised about the reference:
+        delta Y_j = sum_l (dY_j/dX_l) . r_l + sum_l (dY_j/dZ_l) . a_l,
+    so |delta Y_j| <= sum_l |dY_j/dX_l| . 2^-8 |X_l| + sum_l |dY_j/dZ_l| . |a_l|,
+    with dY_j/dX_l from back-propagation through the reference network.
+    Returns (Y_ref [n, 2], bound [n, 2])."""
+    Y, c = reference_forward(theta, X)
+    p, xs, zs = c["p"], c["x"], c["z"]
+    W = [bf16_round(p[f"W{l}"]) for l in range(5)]
+    b = [p[f"b{l}"] for l in range(5)]
+    acc = []   # |a_l|: FP32 accumulation bound of each pre-activation (and of Y)
+    for l in range(5):
+        K = W[l].shape[1] + 1
+        acc.append(K * U_FP32 * (np.abs(xs[l]) @ np.abs(W[l]).T + np.abs(b[l])))
+    bound = np.zeros_like(Y)
+    for j in range(Y.shape[1]):
+        gX = np.tile(W[4][j], (X.shape[0], 1))            # dY_j / dX_4
+        bj = acc[4][:, j] + U_BF16 * np.sum(np.abs(gX) * np.abs(xs[4]), axis=1)
+        for l in range(3, -1, -1):
+            gZ = gX * silu_prime(zs[l])                   # dY_j / dZ_l
+            bj += np.sum(np.abs(gZ) * acc[l], axis=1)
+            gX = gZ @ W[l]                                # dY_j / dX_l
+            if l > 0:
+                bj += U_BF16 * np.sum(np.abs(gX) * np.abs(xs[l]), axis=1)
+        bound[:, j] = bj
+    return Y, bound
+
+
+def gradient_term_scale(theta, X, y):
+    """Sum over the batch of the magnitudes of the terms of every gradient
+    entry of the reference network: for W_l[j, i], sum_n |dZ_l[n, j] X_l[n, i]|;
+    for b_l[j], sum_n |dZ_l[n, j]| (dZ_l = dL/dZ_l of the mean Gaussian NLL).
+    Returns (gradient of the reference network, the scales), both flat in the
+    theta layout."""
+    Y, c = reference_forward(theta, X)
+    L, dY = nll(Y, y)
+    p, xs, zs = c["p"], c["x"], c["z"]
+    W = [bf16_round(p[f"W{l}"]) for l in range(5)]
+    g, sc = {}, {}
+    dz = dY
+    g["W4"], sc["W4"] = dz.T @ xs[4], np.abs(dz).T @ np.abs(xs[4])
+    g["b4"], sc["b4"] = dz.sum(axis=0), np.abs(dz).sum(axis=0)
+    dx = dz @ W[4]
+    for l in range(3, -1, -1):
+        dz = dx * silu_prime(zs[l])
+        g[f"W{l}"], sc[f"W{l}"] = dz.T @ xs[l], np.abs(dz).T @ np.abs(xs[l])
+        g[f"b{l}"], sc[f"b{l}"] = dz.sum(axis=0), np.abs(dz).sum(axis=0)
+        if l > 0:
+            dx = dz @ W[l]
+    return pack(g), pack(sc), L
+
+
 def nll(Y, y):
     """Mean Gaussian NLL over the batch and its gradient with respect to Y."""
     n = Y.shape[0]

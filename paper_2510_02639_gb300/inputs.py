@@ -14,7 +14,7 @@ import numpy as np
 # Default grid (Sec. 3.2-3.3: N_limb ~ 500; polar grid N_r x N_theta per sector).
 DEFAULT_GRID = dict(
     n_r=64, n_theta=256, n_limb=500, n_bins_r=32, n_bins_theta=64,
-    max_iter=100, uniform=0, delta_c=0.02, margin=0.05, img_tol=1e-3,
+    max_iter=100, uniform=0, delta_c=0.02, margin=0.05, img_tol=1e-3, ld_split=0,
 )
 
 
@@ -24,15 +24,15 @@ def grid(**kw) -> dict:
     return g
 
 
-def binary(t0=0.0, tE=20.0, u0=0.01, alpha=0.5, rho=1e-3, u1=0.5, s=1.0, q=1e-3) -> dict:
+def binary(t0=0.0, tE=20.0, u0=0.01, alpha=0.5, rho=1e-3, u1=0.5, s=1.0, q=1e-3, u2=0.0) -> dict:
     return dict(t0=t0, tE=tE, u0=u0, alpha=alpha, rho=rho, u1=u1, n_lens=2, s=s, q=q,
-                q2=0.0, q3=0.0, s2=0.0, s3=0.0, psi=0.0)
+                q2=0.0, q3=0.0, s2=0.0, s3=0.0, psi=0.0, u2=u2)
 
 
 def triple(t0=0.0, tE=30.0, u0=0.005, alpha=2.0, rho=5e-4, u1=0.6,
-           q2=1e-3, q3=3e-4, s2=1.0, s3=0.8, psi=1.2) -> dict:
+           q2=1e-3, q3=3e-4, s2=1.0, s3=0.8, psi=1.2, u2=0.0) -> dict:
     return dict(t0=t0, tE=tE, u0=u0, alpha=alpha, rho=rho, u1=u1, n_lens=3, s=0.0, q=0.0,
-                q2=q2, q3=q3, s2=s2, s3=s3, psi=psi)
+                q2=q2, q3=q3, s2=s2, s3=s3, psi=psi, u2=u2)
 
 
 def caustic_crossing_binary(n_epochs: int = 500):

@@ -65,6 +65,33 @@ def single_lens_ld_disk(u: float, rho: float, u1: float, n_phi: int = 200, n_lim
     return val + I0 * u1 * tot
 
 
+def single_lens_quadratic_ld_disk(u: float, rho: float, u1: float, u2: float, n_phi: int = 200,
+                                  n_limb: int = 4000) -> float:
+    """Quadratically limb-darkened disk, I = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2],
+    mu = sqrt(1 - r~^2), I0 = 1 / (pi (1 - u1/3 - u2/6)), by the same
+    superposition of uniform disks (r~ = sin phi, mu = cos phi, dI/dmu =
+    I0 [u1 + 2 u2 (1 - mu)]):
+      A = I(1) pi A_U(u, rho) + int_0^{pi/2} I0 [u1 + 2 u2 (1 - cos phi)] sin(phi) pi sin^2(phi)
+                                 A_U(u, rho sin phi) dphi."""
+    I0 = 1.0 / (np.pi * (1.0 - u1 / 3.0 - u2 / 6.0))
+    val = I0 * (1.0 - u1 - u2) * np.pi * single_lens_uniform_disk(u, rho, n_limb)
+    edges = [0.0, np.pi / 2]
+    if u < rho:
+        edges = [0.0, np.arcsin(u / rho), np.pi / 2]
+    x, wts = np.polynomial.legendre.leggauss(n_phi)
+    tot = 0.0
+    for a, b in zip(edges[:-1], edges[1:]):
+        ph = 0.5 * (b - a) * x + 0.5 * (b + a)
+        ww = 0.5 * (b - a) * wts
+        for p, wgt in zip(ph, ww):
+            r = rho * np.sin(p)
+            if r <= 0:
+                continue
+            dIdmu = I0 * (u1 + 2.0 * u2 * (1.0 - np.cos(p)))
+            tot += wgt * dIdmu * np.sin(p) * np.pi * np.sin(p) ** 2 * single_lens_uniform_disk(u, r, n_limb)
+    return val + tot
+
+
 def lens_map(eps, a, z):
     """w = z - sum_i eps_i / conj(z - a_i)."""
     z = np.asarray(z, dtype=complex)

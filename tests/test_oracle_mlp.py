@@ -155,3 +155,45 @@ def test_limb_roughness_single_lens_closed_form(oracle_mod):
         assert rough == (H_cf > M.ROUGH_MAX), (u_over_rho, H_cf)
         seen.add(rough)
     assert seen == {True, False}
+
+
+def test_inference_bound_covers_random_activation_roundings():
+    """The first-order bound of inference_bound holds for a network whose
+    hidden activations are perturbed by random relative errors of at most
+    2^-8 (the BF16 rounding it models): a dropped layer or a wrong sign in
+    the back-propagated sensitivities would let a perturbation escape."""
+    rng = np.random.default_rng(3)
+    th = M.init_theta(4).astype(np.float64) + 0.02 * rng.standard_normal(M.N_PARAMS)
+    X = rng.uniform(-1, 1, (400, 7))
+    Yr, bound = M.inference_bound(th, X)
+    p = M.unpack(th)
+    worst = 0.0
+    for trial in range(20):
+        x = M.bf16_round(X)
+        for l in range(4):
+            z = x @ M.bf16_round(p[f"W{l}"]).T + p[f"b{l}"]
+            x = M.silu(z)
+            x = x * (1.0 + M.U_BF16 * rng.choice([-1.0, 1.0], x.shape) * rng.uniform(0.5, 1.0, x.shape))
+        Y = x @ M.bf16_round(p["W4"]).T + p["b4"]
+        worst = max(worst, float(np.max(np.abs(Y - Yr) / bound)))
+    assert worst <= 1.05, worst
+    assert worst >= 0.05, worst   # the bound is not vacuous
+
+
+def test_reference_gradient_is_the_plain_backward_on_rounded_values():
+    """gradient_term_scale's gradient equals the FD-pinned plain backward of
+    the network whose weights and inputs are already BF16 values."""
+    rng = np.random.default_rng(6)
+    th = M.init_theta(7).astype(np.float64) + 0.02 * rng.standard_normal(M.N_PARAMS)
+    d = M.unpack(th)
+    for l in range(5):
+        d[f"W{l}"] = M.bf16_round(d[f"W{l}"])
+    thr = M.pack(d)
+    X = M.bf16_round(rng.uniform(-1, 1, (64, 7)))
+    y = rng.standard_normal(64)
+    gr, sc, L = M.gradient_term_scale(thr, X, y)
+    Y, cache = M.forward(thr, X, bf16=False)
+    L2, dY = M.nll(Y, y)
+    np.testing.assert_allclose(gr, M.backward(cache, dY), rtol=1e-12, atol=1e-15)
+    assert L == pytest.approx(L2, rel=1e-14)
+    assert np.all(sc >= np.abs(gr) - 1e-15)

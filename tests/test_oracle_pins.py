@@ -180,6 +180,30 @@ def test_limb_darkened_disk(oracle_mod, u_over_rho, rho, u1):
     assert abs(A[0, 0] / ref - 1.0) < 1e-4, (A, ref)
 
 
+def test_quadratic_law_reduces_to_linear():
+    """The quadratic superposition integral with u2 = 0 is the linear one."""
+    for u, rho, u1 in ((0.15, 0.05, 0.5), (0.02, 0.05, 0.6)):
+        assert CF.single_lens_quadratic_ld_disk(u, rho, u1, 0.0) == pytest.approx(
+            CF.single_lens_ld_disk(u, rho, u1), rel=1e-12)
+
+
+@pytest.mark.parametrize("u_over_rho,rho,u1,u2,split", [
+    (3.0, 0.05, 0.4, 0.25, 0), (0.5, 0.05, 0.3, 0.3, 0), (2.0, 5e-3, 0.5, 0.2, 0),
+    (3.0, 0.05, 0.4, 0.25, 1), (0.5, 0.05, 0.3, 0.3, 1), (2.0, 5e-3, 0.5, 0.2, 1)])
+def test_quadratic_limb_darkened_disk(oracle_mod, u_over_rho, rho, u1, u2, split):
+    """(iii) Quadratic limb darkening (u2 != 0), single-lens limit, with the
+    literal per-point rule (f(delta) on the whole brightness) and the
+    split-profile rule (the limb value with f_U, the rest with f): both
+    converge to the superposition-of-uniform-disks integral, which pins the
+    law, its normalisation I0 = 1/(pi (1 - u1/3 - u2/6)) and the limb value."""
+    u = u_over_rho * rho
+    p = dict(far_single(rho=rho, u1=u1), u2=u2)
+    g = I.grid(n_r=512, n_theta=2048, n_limb=1000, ld_split=split)
+    A, st = oracle_mod.magnification(p, [u], g)
+    ref = CF.single_lens_quadratic_ld_disk(u, rho, u1, u2)
+    assert abs(A[0, 0] / ref - 1.0) < 1e-4, (A, ref)
+
+
 @pytest.mark.parametrize("case", [
     dict(q=0.2, s=1.0, w=0.02 + 0.01j, uniform=1, u1=0.0),
     dict(q=0.05, s=1.3, w=0.3 - 0.05j, uniform=0, u1=0.5),
