@@ -240,12 +240,13 @@ def timed_steps(fn, steps, warmup, flush, stream):
     return [a.elapsed_time(b) for a, b in ev]
 
 
-def chi2_bench(icrs, I, args, dev, stream, flush, n_sets):
+def chi2_bench(icrs, I, args, dev, stream, flush, n_sets, grid=None):
     """Timed icrs_chi2_grad steps over the adjoint batch (first n_sets sets)."""
     import torch
+    grid = grid or I.grid(**FIXED_GRID)
     params, t, centre, noise = I.adjoint_batch()
     params, t, noise = params[:n_sets], t[:n_sets], noise[:n_sets]
-    g = icrs.grid_from_dict(I.grid(**FIXED_GRID), 2)
+    g = icrs.grid_from_dict(grid, 2)
     pd = icrs.params_to_device(params, dev)
     tt = torch.tensor(t, dtype=torch.float64, device=dev)
     # data: magnification of the centre parameters plus Gaussian noise (F = A)
@@ -263,8 +264,68 @@ def chi2_bench(icrs, I, args, dev, stream, flush, n_sets):
     return {"value": len(params) * args.steps / sec, "unit": "chi^2 gradients/s",
             "epochs_per_s": len(params) * t.shape[1] * args.steps / sec,
             "ms_per_step": sec / args.steps * 1e3, "steps": args.steps, "warmup": args.warmup,
-            "workload": f"adjoint_batch_{len(params)}x{t.shape[1]}", "grid": grid_desc(FIXED_GRID), "params": 8,
+            "workload": f"adjoint_batch_{len(params)}x{t.shape[1]}", "grid": grid_desc(grid), "params": 8,
             "dtype": "f32", "finite": bool(torch.isfinite(grad).all().item()), "gpu_launches": args.steps}
+
+
+def chi2_accuracy(icrs, I, dev, grid, n_epochs=12):
+    """Largest error of icrs_chi2_grad against the oracle's FP64 forward mode
+    (chi^2 gradient of one adjoint-batch set on n_epochs of its epochs),
+    per parameter relative to the oracle's sum_e |dchi2_e/dp|."""
+    import torch
+    import oracle
+    params, t, centre, noise = I.adjoint_batch(n_sets=1)
+    idx = np.linspace(0, t.shape[1] - 1, n_epochs).astype(int)
+    # epochs around the peak, where the finite source matters
+    idx = np.clip(idx // 8 + t.shape[1] * 7 // 16, 0, t.shape[1] - 1)
+    ts = np.ascontiguousarray(t[:, idx])
+    Ao, dAo, _ = oracle.magnification_fwd(params, ts, grid)
+    Ac, _ = oracle.magnification([centre], ts, grid)
+    y = Ac + noise[:, idx]
+    sig = np.full_like(y, 0.01)
+    r = (y - Ao) / sig
+    w = -2.0 * r / sig                                # dchi2/dA per epoch
+    go = (w[0][:, None] * dAo[0]).sum(0)
+    scale = (np.abs(w[0])[:, None] * np.abs(dAo[0])).sum(0)
+    chi2, grad, A, st = icrs.chi2_grad(icrs.params_to_device(params, dev), torch.tensor(ts, device=dev),
+                                       icrs.grid_from_dict(grid, 2), torch.tensor(y, device=dev),
+                                       torch.tensor(sig, device=dev))
+    g = grad.cpu().numpy()[0]
+    return {"epochs": int(len(idx)), "max_rel_err_vs_oracle_fwd": float(np.max(np.abs(g - go) / scale)),
+            "A_max_rel_err": float(np.max(np.abs(A.cpu().numpy() / Ao - 1.0))),
+            "reference": f"oracle FP64 forward mode at {grid['n_r']}x{grid['n_theta']}; error of each component "
+                         "over sum_e |dchi2_e/dp|"}
+
+
+def nll_bench(icrs, I, args, dev, stream, flush, n_sets, grid):
+    """Timed icrs_marginal_nll_grad steps (linear-flux marginalised likelihood
+    and its gradient, one derivative launch plus one reduction) over the
+    adjoint batch with F = (A - 1) F_S + F_base + noise, F_S = F_base = 1."""
+    import torch
+    params, t, centre, noise = I.adjoint_batch()
+    params, t, noise = params[:n_sets], t[:n_sets], noise[:n_sets]
+    g = icrs.grid_from_dict(grid, 2)
+    pd = icrs.params_to_device(params, dev)
+    tt = torch.tensor(t, dtype=torch.float64, device=dev)
+    Ac, _ = icrs.magnification(icrs.params_to_device([centre] * len(params), dev), tt, g)
+    F = (Ac + torch.tensor(noise, device=dev)).contiguous()
+    sig = torch.full_like(F, 0.01)
+    prior = torch.tensor([[1.0, 1.0, 0.25, 0.25]] * len(params), dtype=torch.float64, device=dev)
+    ws = torch.empty(int(icrs.lib.icrs_marginal_nll_workspace_bytes(len(params), t.shape[1])), dtype=torch.uint8,
+                     device=dev)
+    out = {}
+
+    def step():
+        out["r"] = icrs.marginal_nll_grad(pd, tt, g, F, sig, prior, workspace=ws, stream=stream)
+
+    ms = timed_steps(step, args.steps, args.warmup, flush, stream)
+    sec = float(np.sum(ms)) / 1e3
+    nll, grad, fl = out["r"][0], out["r"][1], out["r"][2]
+    return {"value": len(params) * args.steps / sec, "unit": "marginal NLL gradients/s",
+            "epochs_per_s": len(params) * t.shape[1] * args.steps / sec,
+            "ms_per_step": sec / args.steps * 1e3, "workload": f"adjoint_batch_{len(params)}x{t.shape[1]}",
+            "grid": grid_desc(grid), "params": 8, "finite": bool(torch.isfinite(grad).all().item()),
+            "flux_posterior_mean": [float(x) for x in fl.mean(0).tolist()], "gpu_launches": 2 * args.steps}
 
 
 def surrogate_bench(args, dev):
@@ -354,6 +415,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=6, help="oracle epochs per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chi2-sets", type=int, default=256, help="sets of the adjoint batch per chi^2 step (0: skip)")
+    ap.add_argument("--chi2-sets-qualified", type=int, default=8,
+                    help="sets of the adjoint batch per chi^2 step at the headline grid (0: skip)")
     ap.add_argument("--sur-train-sets", type=int, default=200, help="surrogate training sets x 2000 epochs (0: skip)")
     ap.add_argument("--sur-query-sets", type=int, default=250, help="surrogate scoring sets x 2000 epochs")
     ap.add_argument("--sur-epochs", type=int, default=30)
@@ -468,6 +531,14 @@ def main():
              "accuracy": accuracy(icrs, I, gf, dev) if args.workload == "batch" else None}
 
     chi2 = chi2_bench(icrs, I, args, dev, stream, flush, args.chi2_sets) if args.chi2_sets > 0 else None
+    chi2_q = None
+    if args.chi2_sets_qualified > 0:
+        gq = I.grid(**HEADLINE_GRID)
+        chi2_q = chi2_bench(icrs, I, args, dev, stream, flush, args.chi2_sets_qualified, grid=gq)
+        if rank == 0 and not args.no_cpu_baseline:
+            chi2_q["accuracy"] = chi2_accuracy(icrs, I, dev, gq)
+    nll = nll_bench(icrs, I, args, dev, stream, flush, args.chi2_sets, I.grid(**FIXED_GRID)) \
+        if args.chi2_sets > 0 else None
     sur = surrogate_bench(args, dev) if (args.sur_train_sets > 0 and args.workload == "batch" and rank == 0) else None
 
     clocks = clk.summary() if rank == 0 else None
@@ -493,6 +564,8 @@ def main():
         "e2e": e2e,
         "fixed_grid": fixed,
         "chi2_grad": chi2,
+        "chi2_grad_qualified_grid": chi2_q,
+        "marginal_nll_grad": nll,
         "surrogate": sur,
         "clocks": clocks,
         "gpu_launches": args.steps,

@@ -66,7 +66,10 @@ extern "C" {
  *               w_c(t) = tau (cos a, sin a) + u0 (-sin a, cos a),
  *               tau = (t - t0) / tE                       (Sec. 3.5, Fig. 3)
  *   rho         source radius in Einstein radii (> 0)
- *   u1          linear limb-darkening coefficient in [0, 1) (Appendix A.2)
+ *   u1          linear limb-darkening coefficient (Appendix A.2)
+ *   u2          quadratic limb-darkening coefficient (0: the linear law of
+ *               Appendix A.2): I = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2],
+ *               mu = sqrt(1 - d^2/rho^2), I0 = 1 / (pi (1 - u1/3 - u2/6))
  *   n_lens      2 (binary) or 3 (triple)
  *   binary:     s = separation, q = m2/m1 (> 0); masses eps1 = 1/(1+q),
  *               eps2 = q/(1+q); lenses on the real axis with the primary at
@@ -81,6 +84,7 @@ typedef struct {
   int32_t reserved;
   double s, q;
   double q2, q3, s2, s3, psi;
+  double u2;
 } icrs_params;
 
 /*
@@ -90,17 +94,28 @@ typedef struct {
  *   n_bins_r       radial bins per angular interval: 2..32
  *   n_bins_theta   angular bins over [-pi, pi): 2..64
  *   max_iter       cap on root iterations
- *   uniform        1: uniform source (Appendix A.1 rule), 0: linear LD
+ *   uniform        1: uniform source (Appendix A.1 rule), 0: limb darkening
+ *                  (u1, u2 of the parameter set)
  *   delta_c        threshold of the LD correction f(delta) (Appendix A.2), > 0
  *   margin         sector widening, fraction of the extent per side (>= 0)
  *   img_tol        lens-equation residual below which a root is an image
  *   n_lens         see the field comment
+ *   ld_split       0: the boundary points' weight f(delta) multiplies the whole
+ *                  brightness (Appendix A.2); 1: split-profile rule (a
+ *                  variant): the limb value I_limb = I0 (1 - u1 - u2), which
+ *                  jumps to zero across the edge, takes the uniform weight
+ *                  f_U(delta) = delta + 1/2, and I - I_limb, which vanishes at
+ *                  the edge like a square root, takes f(delta).  Forward
+ *                  entry points only (the derivative ones return
+ *                  ICRS_EUNSUPPORTED).
  */
 typedef struct {
   int32_t n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter, uniform;
   int32_t n_lens;  /* lens count shared by every set of the call (2 or 3); 0 = read it
                       from the first set on the device, which synchronises `stream` */
   double delta_c, margin, img_tol;
+  int32_t ld_split;
+  int32_t reserved;
 } icrs_grid;
 
 /* Fills `g` with the library defaults (64 x 256 grid, 500 limb points, 32 x 64
@@ -204,6 +219,42 @@ int icrs_chi2_grad(const icrs_params* p, int S, const double* t, int E,
                    const icrs_grid* g, const double* y, const double* sigma,
                    double* chi2, double* grad, double* A, uint32_t* status,
                    void* stream);
+
+/*
+ * Linear-flux marginalised likelihood of S light curves (Appendix B) and its
+ * gradient with respect to the 8 parameters of icrs_magnification_vjp.
+ * Light curve s is F[s][e] = (A[s][e] - 1) F_S + F_base + noise, noise ~
+ * N(0, sigma[s][e]^2), with the prior (F_S, F_base) ~ N(mu, diag(lambda)).
+ * Marginalising the fluxes (Eq. NLL, evaluated with the Woodbury identity
+ * printed after it):
+ *     nll[s] = 1/2 (F - M mu)^T B^-1 (F - M mu) + 1/2 ln|B|,
+ *     B = C + M Lambda M^T,  M = [A - 1, 1],  C = diag(sigma^2)
+ * (no n/2 ln 2 pi term, as printed).  The gradient chains
+ *     dnll/dA_e = c_e [(K^-1 m_e)_0 - (F_e - m_e . a) a_0],
+ *     K = Lambda^-1 + M^T C^-1 M,  c_e = sigma_e^-2,  m_e = (A_e - 1, 1),
+ * with a = mu + K^-1 M^T C^-1 (F - M mu) the posterior mean of (F_S,
+ * F_base), through the per-epoch derivative dA/dp of the adjoint kernel.
+ *   F, sigma  [S][E] device double: fluxes and their errors (sigma > 0)
+ *   prior     [S][4] device double: mu_S, mu_base, lambda_S, lambda_base
+ *             (prior means and variances, variances > 0)
+ *   nll       [S] device double (out)
+ *   grad      [S][8] device double or NULL (out).  NULL: the likelihood only
+ *             (one forward launch); otherwise one derivative launch (binary
+ *             lens; a triple lens returns ICRS_EUNSUPPORTED)
+ *   fluxes    [S][2] device double or NULL (out): the posterior mean a
+ *   A, status optional outputs, as icrs_magnification
+ *   workspace device memory of icrs_marginal_nll_workspace_bytes(S, E)
+ *             bytes, 8-byte aligned, caller-owned (per-epoch dA/dp and A)
+ * The per-set sums run in a fixed order in FP64 (one block per set), so the
+ * results do not depend on scheduling.  A non-positive sigma or prior
+ * variance gives a NaN nll for that set.
+ */
+size_t icrs_marginal_nll_workspace_bytes(int S, int E);
+int icrs_marginal_nll_grad(const icrs_params* p, int S, const double* t, int E,
+                           const icrs_grid* g, const double* F, const double* sigma,
+                           const double* prior, double* nll, double* grad, double* fluxes,
+                           double* A, uint32_t* status, void* workspace,
+                           size_t workspace_bytes, void* stream);
 
 /*
  * ICRS on a list of items of an [S][E] problem: for i < n, item items[i] =
@@ -318,6 +369,25 @@ int icrs_surrogate_features(const icrs_params* p, int S, const double* t, int E,
                             const icrs_grid* g, float* features, double* A_ps,
                             uint32_t* status, void* stream);
 
+/*
+ * Training target of the network for n epochs:
+ *     target[i] = 1e4 log(A[i] / A_ps[i]) - features[i][7]
+ * (FP64, rounded to float), from ICRS magnifications A and the feature
+ * kernel's A_ps and second-order estimate b.
+ *   A, A_ps [n] device double; features [n][8] device float; target [n] out
+ */
+int icrs_surrogate_target(const double* A, const double* A_ps, const float* features, int n,
+                          float* target, void* stream);
+
+/*
+ * Mini-batch gather for training: out_features[i] = features[idx[i]] and
+ * out_target[i] = target[idx[i]] for i < n.  The permutation idx (device
+ * int32, entries in range) is drawn by the caller.  features and
+ * out_features must be 16-byte aligned.
+ */
+int icrs_surrogate_batch(const float* features, const float* target, const int32_t* idx, int n,
+                         float* out_features, float* out_target, void* stream);
+
 /* Bytes of workspace icrs_surrogate_gate needs for n epochs. */
 size_t icrs_surrogate_gate_workspace_bytes(int n);
 
@@ -343,6 +413,32 @@ int icrs_surrogate_gate(const float* pred, const float* features, const double* 
                         float b_max, float caustic_min, double A_max, float rho_min, double A_small,
                         double* A, int32_t* routed_idx, int32_t* n_routed,
                         void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Non-learned epoch preselection: the control for the learned gate.  Sec.
+ * 3.4 (iii) runs the extended-source computation only on a preselected set
+ * of epochs near caustics.  Epoch e of light curve s (item q = s * E + e of
+ * an [S][E] problem) is near a caustic unless all of these hold:
+ *   - its feature status is 0 (as in icrs_surrogate_gate);
+ *   - features[q][6] >= caustic_min;
+ *   - |features[q][7]| <= b_max (the second-order estimate b);
+ *   - A_ps[q] <= A_max, or <= A_small when rho < rho_min.
+ * Every epoch of the same light curve within n_ext epochs of a near-caustic
+ * epoch is routed to ICRS as well (the caustic can fall between epochs).
+ * The remaining epochs get a finite-source estimate without ray shooting:
+ *   mode 0: A = A_ps (point source);
+ *   mode 1: A = A_ps exp(1e-4 features[q][7]) (second-order estimate).
+ * Routed items are listed in increasing order in routed_idx[0 .. *n_routed)
+ * and their A is left for icrs_magnification_indexed.
+ *   features [S*E][8], A_ps [S*E], st_ps [S*E]: from icrs_surrogate_features
+ *   workspace  device, >= icrs_epoch_gate_workspace_bytes(S, E)
+ * S * E must fit in an int32 (else ICRS_EUNSUPPORTED).
+ */
+size_t icrs_epoch_gate_workspace_bytes(int S, int E);
+int icrs_epoch_gate(const float* features, const double* A_ps, const uint32_t* st_ps, int S, int E,
+                    int n_ext, int mode, float b_max, float caustic_min, double A_max, float rho_min,
+                    double A_small, double* A, int32_t* routed_idx, int32_t* n_routed,
+                    void* workspace, size_t workspace_bytes, void* stream);
 
 /* Message for a return code (static string). */
 const char* icrs_strerror(int code);

@@ -306,4 +306,39 @@ __device__ inline int ehrlich_aberth_f32(const cf* b, cf* z, int max_iter, float
   return -1;
 }
 
+// Ehrlich-Aberth iteration in FP64 (Sec. 3.1): the fallback for positions
+// whose FP32 roots do not give a trustworthy image set (clusters of close
+// roots next to a critical curve, which FP32 cannot separate).  Stops when every step is
+// below 1e-14 max(1, |z|) or twice the FP64 rounding level of P at the root.
+template <int N>
+__device__ inline int ehrlich_aberth_f64(const cd* b, cd* z, int max_iter) {
+  double ab[N + 1];
+  for (int l = 0; l <= N; ++l) ab[l] = sqrt(abs2(b[l]));
+  for (int it = 0; it < max_iter; ++it) {
+    cd dz[N];
+    double noise[N];
+    bool done = true;
+    for (int k = 0; k < N; ++k) {
+      cd p, dp;
+      horner2<N, double>(b, z[k], p, dp);
+      double az = sqrt(abs2(z[k])), pa = ab[N];
+      for (int l = N - 1; l >= 0; --l) pa = fma(pa, az, ab[l]);
+      noise[k] = 1.1102230246251565e-16 * pa / fmax(sqrt(abs2(dp)), 1e-300);
+      cd W = dv(p, dp);
+      cd S = mk(0.0, 0.0);
+      for (int j = 0; j < N; ++j)
+        if (j != k) S = S + inv(z[k] - z[j]);
+      dz[k] = dv(W, mk(1.0, 0.0) - W * S);
+      if (!(abs2(p) > 0.0)) dz[k] = mk(0.0, 0.0);
+    }
+    for (int k = 0; k < N; ++k) {
+      z[k] = z[k] - dz[k];
+      double st = sqrt(abs2(dz[k]));
+      if (!(st <= fmax(1e-14 * fmax(1.0, sqrt(abs2(z[k]))), 2.0 * noise[k]))) done = false;
+    }
+    if (done) return it + 1;
+  }
+  return -1;
+}
+
 }  // namespace icrs

@@ -33,18 +33,20 @@
 #include "icrs_common.cuh"
 #include "icrs_df64.cuh"
 #include "icrs_sectors.cuh"
+#include "icrs_ps.cuh"
 
 namespace icrs {
 
-// Threads per block (one block per SM).  The binary forward kernel prefers
-// 768 threads: its root phases fit in 80 registers with small spills, and
-// the ray stage, bound by instruction issue and dependency latency, gains
-// from the 24 warps per SM (+19% over 512 at the 1024 x 2048 grid).  Where
-// the wider layout's per-warp buffers do not fit in shared memory (n_theta
-// = 8192 at N_limb = 500), it falls back to a 512-thread instantiation.  The
-// derivative and triple instantiations keep 512 threads (128 registers): at
-// 80 their FP64 phases spill kilobytes.
-constexpr int NT_WIDE = 768, NT_BASE = 512;
+// Threads per block (one block per SM).  The binary forward kernel runs 640
+// threads (96 registers): its ray stage keeps a whole column step in
+// registers and is bound by instruction issue and dependency latency, so it
+// gains from more warps (at 1024 x 2048: 512 threads 13.7 ms, 576 12.8 ms,
+// 640 11.8 ms on a 320-epoch sample), but at 704 threads (88 registers) it
+// spills and takes 21 ms.  Where the wider layout does not fit in shared
+// memory it falls back to a 512-thread instantiation.  The derivative and
+// triple instantiations keep 512 threads (128 registers): with fewer their
+// FP64 phases spill kilobytes.
+constexpr int NT_WIDE = 640, NT_BASE = 512;
 __host__ __device__ constexpr int mag_threads(int nl, bool der) { return (nl == 2 && !der) ? NT_WIDE : NT_BASE; }
 constexpr int NW_MAX = NT_WIDE / 32;  // warps per block, largest instantiation
 constexpr int NW_DER = NT_BASE / 32;  // warps per block, derivative mode
@@ -55,16 +57,20 @@ constexpr int MAXRB = 32;        // r bins per theta run
 constexpr int MAXCELL = 96;      // (theta run, r run) cells
 constexpr int MAXBOX = 96;       // candidate sectors before merging
 constexpr int MAXANCH = 128;     // FP64 anchors per sector
+constexpr int GTH_MAX = 256;     // columns per theta group (at most)
 constexpr int MAXCELL_D = 32;    // cells with tracked derivatives
 constexpr int MAXBOX_D = 32;     // candidate sectors with tracked derivatives
 constexpr float TINY_EXTENT = 3e-4f;  // images smaller than this x rho skip FP64 decisions
 constexpr float EPS32 = 5.9604645e-8f;  // 2^-24
+// A refined FP32 image whose error bound exceeds EE_SUSPECT max(1, r), or two
+// images of one limb point closer than DUP_TOL max(1, r), send the limb point
+// to the FP64 re-solve.
+constexpr float EE_SUSPECT = 1e-6f;
+constexpr float DUP_TOL = 1e-6f;
 
-// Rays per row segment.  Forward: 508, so that a segment and its 4-ray halo
-// fill exactly 8 iterations of 32 lanes x 2 rays, with row buffers small
-// enough to leave room for an FP64 point table of 1024 (768 threads) to 2500
-// entries at n_theta = 2048.  Derivative mode: 256 (its per-ray seeds take the
-// same room again).
+// Rays per row segment of the derivative mode's row buffers: 256 (its per-ray
+// seeds take the same room again).  (The forward ray stage keeps no row
+// buffer.)
 __host__ __device__ __forceinline__ int row_segment(int n_theta, bool der) {
   const int segmax = der ? 256 : 508;
   return n_theta < segmax ? n_theta : segmax;
@@ -79,6 +85,8 @@ struct Anchor {
   cf K[3];      // eps_j / A_j
   float e0;     // error bound constant part
   float e1;     // error bound factor of |U|_1
+  float lo2;    // below: every ray of the group is inside the source (FP32 certain)
+  float hi2;    // above: every ray of the group is outside (FP32 certain)
 };
 
 using Box = BoxT<double>;
@@ -86,7 +94,7 @@ using Box = BoxT<double>;
 struct Shared {
   // ---- per parameter set
   Lens L;
-  double rho, u1;
+  double rho, u1, u2;
   float eps32[3];
   cf aj32[3][3];       // [frame j][lens i]: a_i - a_j (FP32)
   cf D32[3][4], E32[3][3];  // polynomial parts in frame j (FP32)
@@ -130,6 +138,8 @@ struct Shared {
   double dr64, dth64;
   float dr32, dth32;
   int nanch;
+  int task_ctr;        // next (row block, theta chunk) task of the forward ray stage
+  int chunk;           // columns per theta chunk
   double red[NW_MAX];
 };
 
@@ -211,8 +221,13 @@ __device__ inline void polish_image64(const Shared& sh, cd z0, cd w, double* r, 
 // FP64 validation of an ambiguous root: Newton's method on the polynomial
 // written about the root's nearest lens, then the lens-equation residual in
 // that frame against img_tol.  Returns 1 (image) or 0; (r, theta) if image.
+// *conv (if given) is cleared when the Newton steps had not converged: next to
+// a near-double root Newton converges only linearly, and an iterate still
+// ~1e-4 from the root can pass the residual test there (the lens map is flat
+// across the critical curve).
 template <int NL>
-__device__ inline int validate_root64(const Shared& sh, cd z0, cd w, double img_tol, double* r, double* th) {
+__device__ inline int validate_root64(const Shared& sh, cd z0, cd w, double img_tol, double* r, double* th,
+                                      int* conv = nullptr) {
   constexpr int N = NL * NL + 1;
   int j = nearest_lens64<NL>(sh.L, z0);
   double eps[NL];
@@ -223,14 +238,16 @@ __device__ inline int validate_root64(const Shared& sh, cd z0, cd w, double img_
   cd wj = w - sh.L.a[j];
   lens_poly<NL, double>(eps, a, D, E, wj, b);
   cd x = z0 - sh.L.a[j];
+  bool done = false;
   for (int it = 0; it < 8; ++it) {
     cd p, dp;
     horner2<N, double>(b, x, p, dp);
     if (!(abs2(dp) > 0.0)) break;
     cd st = dv(p, dp);
     x = x - st;
-    if (abs2(st) <= 1e-30 * fmax(1.0, abs2(x))) break;
+    if (abs2(st) <= 1e-30 * fmax(1.0, abs2(x))) { done = true; break; }
   }
+  if (conv) *conv = done ? 1 : 0;
   cd F = lens_map<NL, double>(eps, a, x) - wj;
   double res = sqrt(abs2(F));
   if (!(res <= img_tol)) return 0;
@@ -238,41 +255,6 @@ __device__ inline int validate_root64(const Shared& sh, cd z0, cd w, double img_
   *r = sqrt(z.x * z.x + z.y * z.y);
   *th = atan2(z.y, z.x);
   return 1;
-}
-
-// Ehrlich-Aberth iteration in FP64 (Sec. 3.1): the fallback for limb points
-// whose FP32 roots give an illegal image count (clusters of close roots next
-// to a critical curve, which FP32 cannot separate).  Stops when every step is
-// below 1e-14 max(1, |z|) or twice the FP64 rounding level of P at the root.
-template <int N>
-__device__ inline int ehrlich_aberth_f64(const cd* b, cd* z, int max_iter) {
-  double ab[N + 1];
-  for (int l = 0; l <= N; ++l) ab[l] = sqrt(abs2(b[l]));
-  for (int it = 0; it < max_iter; ++it) {
-    cd dz[N];
-    double noise[N];
-    bool done = true;
-    for (int k = 0; k < N; ++k) {
-      cd p, dp;
-      horner2<N, double>(b, z[k], p, dp);
-      double az = sqrt(abs2(z[k])), pa = ab[N];
-      for (int l = N - 1; l >= 0; --l) pa = fma(pa, az, ab[l]);
-      noise[k] = 1.1102230246251565e-16 * pa / fmax(sqrt(abs2(dp)), 1e-300);
-      cd W = dv(p, dp);
-      cd S = mk(0.0, 0.0);
-      for (int j = 0; j < N; ++j)
-        if (j != k) S = S + inv(z[k] - z[j]);
-      dz[k] = dv(W, mk(1.0, 0.0) - W * S);
-      if (!(abs2(p) > 0.0)) dz[k] = mk(0.0, 0.0);
-    }
-    for (int k = 0; k < N; ++k) {
-      z[k] = z[k] - dz[k];
-      double st = sqrt(abs2(dz[k]));
-      if (!(st <= fmax(1e-14 * fmax(1.0, sqrt(abs2(z[k]))), 2.0 * noise[k]))) done = false;
-    }
-    if (done) return it + 1;
-  }
-  return -1;
 }
 
 // FP64 distance of ray (i, l) of a sector from the source centre, with the
@@ -502,14 +484,16 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   double* pt = (double*)p;       p += sizeof(double) * PMAX;
   int* queue = (int*)p;          p += sizeof(int) * QMAX;
   Anchor* anch = (Anchor*)p;     p += sizeof(Anchor) * MAXANCH;
-  cf* tab = (cf*)p;              p += sizeof(cf) * g.n_theta;
+  cf* tab = (cf*)p;              p += sizeof(cf) * (GTH_MAX + 2);  // group offsets (two float arrays)
   const int seg = row_segment(g.n_theta, DER);  // rays per row segment
-  float* rowbuf = (float*)p;     p += sizeof(float) * NW * (seg + 4);
+  float* rowbuf = (float*)p;     p += DER ? sizeof(float) * NW * (seg + 4) : 0;  // row buffers (derivative mode)
   cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
-  // boundary points of the current row segment; forward binary mode: a
-  // deferred queue of 32 points x 8 words (stencil, row factor, indices)
-  const bool DEFER = !DER && NL == 2 && defer;
-  int* wqueue = (int*)p;         p += sizeof(int) * NW * (DEFER ? 256 : 64);
+  // boundary points: forward mode, a deferred queue per warp of 32 points x
+  // 8 words (stencil, row factor, indices); derivative mode, the indices of
+  // the current row segment's points
+  const bool DEFER = false;
+  (void)defer;
+  int* wqueue = (int*)p;         p += sizeof(int) * NW * (!DER ? 256 : 64);
   // derivative mode: its state and the per-warp ray seeds
   DerShared& ds = *(DerShared*)p;  p += DER ? sizeof(DerShared) : 0;
   DualD* cdual = ds.cx;
@@ -540,6 +524,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         sh.L = make_lens(prm);
         sh.rho = prm.rho;
         sh.u1 = prm.u1;
+        sh.u2 = prm.u2;
         for (int j = 0; j < NL; ++j) {
           sh.eps32[j] = (float)sh.L.eps[j];
           double eps[NL];
@@ -815,9 +800,17 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         cd w = limb_point64(sh, k, K);
         cd z0 = tod(phi[ps]) + sh.L.a[ll];
         double r, th;
-        int ok = validate_root64<NL>(sh, z0, w, g.img_tol, &r, &th);
+        int conv = 1;
+        int ok = validate_root64<NL>(sh, z0, w, g.img_tol, &r, &th, &conv);
         uint8_t m = 0;
-        if (ok) {
+        if (ok && NL == 2 && !conv) {
+          // not converged: kept as an image with an infinite error bound, so
+          // that the limb point goes to the FP64 re-solve below
+          m = M_VALID;
+          const float rh = (float)r;
+          r32[ps] = rh; rl32[ps] = (float)(r - (double)rh); t32[ps] = (float)th;
+          e32[ps] = __int_as_float(0x7f800000);
+        } else if (ok) {
           int pi = atomicAdd(&sh.pn, 1);
           float rh = (float)r;
           if (pi < PMAX) { pr[pi] = r; pt[pi] = th; pidx[ps] = (short)pi; m = M_VALID | M_EXACT; r32[ps] = rh; rl32[ps] = (float)(r - (double)rh); t32[ps] = (float)th; e32[ps] = 0.f; }
@@ -835,10 +828,40 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     auto legal_count = [&](int m) -> bool {
       return (NL == 2) ? (m == 3 || m == 5) : (m == 4 || m == 6 || m == 8 || m == 10);
     };
+    // Binary lens: the same FP64 re-solve takes limb points whose FP32 image
+    // set is not trustworthy although its count is legal: an image whose
+    // refining Newton step left a large error bound (an approximation next to
+    // a critical curve, where det J ~ 0 sends the step far away), or two
+    // slots holding the same image (two approximations that met at one root
+    // while another image was missed).  Without this check the image set, and
+    // so the sectors, could depend on where the iteration started.  (Triple
+    // lens: images beside the small lenses have large second derivatives and
+    // so large bounds, and the FP64 re-solve in the lightest lens's frame is
+    // less accurate there than the two-frame FP32 solve; only illegal counts
+    // are re-solved.)
     for (int k = tid; k < K; k += NT) {
       int m = 0;
-      for (int j = 0; j < N; ++j) m += (meta[k * N + j] & M_VALID) ? 1 : 0;
-      if (!legal_count(m)) q_push(sh, queue, k);
+      bool suspect = false;
+      float zx[N], zy[N];
+      for (int j = 0; j < N; ++j) {
+        const int ps = k * N + j;
+        if (!(meta[ps] & M_VALID)) continue;
+        const bool ex = meta[ps] & M_EXACT;
+        const float r = ex ? (float)pr[pidx[ps]] : r32[ps];
+        const float th = ex ? (float)pt[pidx[ps]] : t32[ps];
+        if (!ex && !(e32[ps] <= EE_SUSPECT * fmaxf(1.0f, r))) suspect = true;
+        float sn, cs;
+        sincosf(th, &sn, &cs);
+        const float x = r * cs, y = r * sn;
+        for (int i2 = 0; i2 < m; ++i2) {
+          const float dx = x - zx[i2], dy = y - zy[i2];
+          const float tol = DUP_TOL * fmaxf(1.0f, r);
+          if (dx * dx + dy * dy <= tol * tol) suspect = true;
+        }
+        zx[m] = x; zy[m] = y;
+        ++m;
+      }
+      if (!legal_count(m) || (NL == 2 && suspect)) q_push(sh, queue, k);
     }
     __syncthreads();
     {
@@ -1284,10 +1307,17 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     if (diag_cnt && tid == 0) { long long c_ = clock64(); sh.cnt[11] = (int)min(c_ - sh.clk0, 2000000000LL); sh.clk0 = c_; }
     // ------------------------------------------------ 9. rays
     const int NR = g.n_r, NTH = g.n_theta;
-    const float u1f = (float)sh.u1;
-    const float I0 = g.uniform ? (float)(1.0 / kPi) : (float)(3.0 / (kPi * (3.0 - sh.u1)));
+    // limb darkening I = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2], mu = sqrt(1 -
+    // d^2/rho^2), I0 = 1 / (pi (1 - u1/3 - u2/6)) (the linear law of
+    // Appendix A.2 when u2 = 0); uniform: I = 1/pi
+    const float I0 = g.uniform ? (float)(1.0 / kPi) : (float)(1.0 / (kPi * (1.0 - sh.u1 / 3.0 - sh.u2 / 6.0)));
     const float irho2 = 1.0f / (rho32 * rho32);
     const float dcf = (float)g.delta_c;
+    // I = c0f + c1f mu + c2f mu^2: c0f = I0 (1 - u1 - u2) is the limb value
+    const float c0f = g.uniform ? I0 : (float)((double)I0 * (1.0 - sh.u1 - sh.u2));
+    const float c1f = g.uniform ? 0.f : (float)((double)I0 * (sh.u1 + 2.0 * sh.u2));
+    const float c2f = g.uniform ? 0.f : (float)(-(double)I0 * sh.u2);
+    const bool split = g.ld_split && !g.uniform;  // split-profile boundary rule
     float acc_s = 0.f, acc_c = 0.f;  // Kahan sum of this thread
     uint32_t st_local = 0u;
     float* buf = rowbuf + warp * (seg + 4);
@@ -1303,13 +1333,25 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         int mth = (int)ceil(B.r_hi * B.width / LMAX);
         int mr = (int)ceil((B.r_hi - B.r_lo) / LMAX);
         mth = min(max(mth, 1), min(64, NTH));
+        // groups of at most GTH_MAX columns (the offset table's size; for
+        // n_theta <= 8192 this needs at most 32 groups)
+        mth = max(mth, (NTH + GTH_MAX - 1) / GTH_MAX);
         mr = min(max(mr, 1), min(4, NR));
         mth = min(mth, MAXANCH / mr);  // the anchor table holds MAXANCH entries
-        sh.gth = (NTH + mth - 1) / mth;
+        // theta groups of an even width: the forward ray stage evaluates
+        // column pairs (l, l + 1), l even, which then share their group
+        sh.gth = 2 * ((NTH + 2 * mth - 1) / (2 * mth));
         sh.gr = (NR + mr - 1) / mr;
         sh.mth = (NTH + sh.gth - 1) / sh.gth;
         sh.mr = (NR + sh.gr - 1) / sh.gr;
         sh.nanch = sh.mth * sh.mr;
+        sh.task_ctr = 0;
+        // forward ray stage: tasks of 32 rows (one per lane) x a theta chunk
+        // of an even number of columns, about 8 tasks per warp per sector
+        // (dynamic assignment)
+        const int nrb = (NR + 31) >> 5;
+        const int nch = max(1, (8 * NW + nrb - 1) / nrb);
+        sh.chunk = min(NTH, max(16, 2 * ((NTH + 2 * nch - 1) / (2 * nch))));
       }
       __syncthreads();
       const int gth = sh.gth, gr = sh.gr, mth = sh.mth;
@@ -1338,16 +1380,45 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         double half = 0.5 * gr * sh.dr64 + (B.r_hi) * 0.5 * gth * sh.dth64;
         an_.e0 = (float)(16.0 * EPS32 * (fabs(an_.ws.x) + fabs(an_.ws.y) + 2.0 * half));
         an_.e1 = (float)(16.0 * EPS32 * half);
+        // the same bound for the whole group: every ray has |dz| <= half, so
+        // |U|_1 <= sqrt(2) sum_j |K_j| / (|A_j| - half); squared distances
+        // outside [lo2, hi2] are decided in FP32 for every ray of the group
+        // (a superset of the per-ray uncertain band, with slack for the FP32
+        // evaluation of that band)
+        {
+          double um = 0.0;
+          bool bounded = true;
+          for (int j = 0; j < NL; ++j) {
+            const double aa = sqrt((double)an_.A[j].x * an_.A[j].x + (double)an_.A[j].y * an_.A[j].y);
+            if (!(aa > 1.0625 * half)) bounded = false;
+            else um += sqrt((double)an_.K[j].x * an_.K[j].x + (double)an_.K[j].y * an_.K[j].y) / (aa - half);
+          }
+          const double rr = (double)rho32 * (double)rho32;
+          const double eb = (double)an_.e0 + (double)an_.e1 * 1.4142135623730951 * um;
+          const double X = 1.01 * (2.0 * (double)rho32 * eb + eb * eb) + 8.0 * EPS32 * rr;
+          if (bounded && X < 0.5 * rr) {
+            an_.lo2 = __double2float_rd(rr - X);
+            an_.hi2 = __double2float_ru(rr + X);
+          } else {
+            an_.lo2 = -1.0f;
+            an_.hi2 = __int_as_float(0x7f800000);
+          }
+        }
         anch[an] = an_;
         if (DER) ds.acs[an] = make_float2((float)cs, (float)sn);
       }
-      // offsets within a theta group: (cos d - 1, sin d), d = (o + 1/2 - gth/2) dth
+      // offsets within a theta group: (cos d - 1, sin d), d = (o + 1/2 - gth/2)
+      // dth, stored as two arrays (tabx, taby) so that a column pair's
+      // offsets load as one 8-byte word each
+      float* tabx = (float*)tab;
+      float* taby = tabx + gth;
       for (int o = tid; o < gth; o += NT) {
         float d = ((float)o + 0.5f - 0.5f * (float)gth) * sh.dth32;
         float s, c;
         sincosf(d, &s, &c);
         float sh2 = sinf(0.5f * d);
-        tab[o] = mk(-2.0f * sh2 * sh2, s);
+        tabx[o] = -2.0f * sh2 * sh2;
+        taby[o] = s;
         (void)c;
       }
       __syncthreads();
@@ -1360,24 +1431,24 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       // inside (W = 1) are summed directly; points next to the image
       // boundary are queued per warp and their crossings solved with one
       // point per lane.
+      // I(d) = c0f + c1f mu + c2f mu^2, mu^2 = x = 1 - d^2/rho^2
       auto brightness = [&](float d2) -> float {
-        if (g.uniform) return I0;
-        float x = fmaxf(0.f, 1.0f - d2 * irho2);
-        float sx = x > 0.f ? x * rsqrtf(x) : 0.f;
-        return I0 * (1.0f - u1f * (1.0f - sx));
+        const float x = fmaxf(fmaf(-d2, irho2, 1.0f), 1e-30f);
+        return fmaf(c2f, x, fmaf(c1f, x * rsqrtf(x), c0f));
       };
-      // I and dI/dd, dI/drho, dI/du1 at squared distance d2 (linear law:
-      // I = I0 (1 - u1 + u1 sqrt(1 - d^2/rho^2)), I0 = 3 / (pi (3 - u1)))
+      // I and dI/dd, dI/drho, dI/du1 at squared distance d2:
+      //   dI/dx = c1/(2 mu) + c2, dx/dd = -2 d/rho^2, dx/drho = 2 d^2/rho^3,
+      //   dI/du1 = I (pi/3) I0 - I0 (1 - mu)   (dI0/du1 = (pi/3) I0^2)
       auto brightness_der = [&](float d2, float* Id, float* Ir, float* Iu) -> float {
         if (g.uniform) { *Id = 0.f; *Ir = 0.f; *Iu = 0.f; return I0; }
         float x = fmaxf(0.f, 1.0f - d2 * irho2);
         float sx = x > 0.f ? x * rsqrtf(x) : 0.f;
-        float I = I0 * (1.0f - u1f * (1.0f - sx));
+        float I = c0f + c1f * sx + c2f * x;
         float d = sqrtf(d2);
-        float k = sx > 0.f ? I0 * u1f * irho2 / sx : 0.f;
+        float k = sx > 0.f ? (c1f / sx + 2.0f * c2f) * irho2 : 0.f;
         *Id = -k * d;
         *Ir = k * d2 / rho32;
-        *Iu = I / (3.0f - u1f) + I0 * (sx - 1.0f);
+        *Iu = I * (float)(kPi / 3.0) * I0 + I0 * (sx - 1.0f);
         return I;
       };
       // derivative mode: per side, d delta / d(stencil distances) and
@@ -1391,12 +1462,15 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       // beyond a non-periodic edge), or NULL to compute them here
       // sv[k] = signed squared distance of ray l - 2 + k (sv[2] is the
       // point), lab = l (absolute index), irow = its row
-      auto boundary_weight = [&](int mi, const float* sv, int lab, int irow, const double* dist) -> float {
+      // WU (forward mode, optional): the same point's weight under the
+      // uniform rule f_U(delta) = delta + 1/2, for the split-profile rule
+      auto boundary_weight = [&](int mi, const float* sv, int lab, int irow, const double* dist,
+                                 float* WU = nullptr) -> float {
         float d2 = -sv[2];
         float vl = sv[1], vr = sv[3];
         bool Lin = signbit(vl), Rin = signbit(vr);
         float W;
-          float fL = 0.f, fR = 0.f;
+          float fL = 0.f, fR = 0.f, uL = 0.f, uR = 0.f;
           if (DER) { sd_n[0] = sd_n[1] = 0; sd_c[0] = sd_c[1] = 0.f; }
           for (int side = 0; side < 2; ++side) {
             bool isL = side == 0;
@@ -1501,13 +1575,14 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                 double dd = isL ? -xd : xd;
                 delta = (float)dd;
                 float fv = (float)fdelta<double>(dd, g.delta_c, 0);
-                if (isL) fL = fv; else fR = fv;
+                if (isL) { fL = fv; uL = delta + 0.5f; } else { fR = fv; uR = delta + 0.5f; }
                 continue;
               }
             }
             float fv = fdelta<float>(delta, dcf, g.uniform);
-            if (isL) fL = fv; else fR = fv;
+            if (isL) { fL = fv; uL = delta + 0.5f; } else { fR = fv; uR = delta + 0.5f; }
           }
+          if (WU) *WU = Lin ? uR : (Rin ? uL : fmaxf(0.f, uL + uR - 1.0f));
           if (Lin) W = fR;
           else if (Rin) W = fL;
           else W = fmaxf(0.f, fL + fR - 1.0f);
@@ -1531,6 +1606,226 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         __syncwarp();
         dq_n = 0;
       };
+      if constexpr (!DER) {
+        // ---- forward ray stage.  A warp takes a task of 32 rows (lane = row
+        // i) and a chunk [c0, c1) of theta columns, and sweeps the columns in
+        // order (all lanes at the same column, so the group offset table and,
+        // within an r group, the anchor are shared).  Each ray's squared
+        // distance is decided inside / outside in registers; the last five
+        // distances stay in a register ring, and a window of inside flags
+        // finds boundary points (inside with an outside neighbour), which go
+        // with their stencil to the per-warp deferred queue.  Every inside ray
+        // adds I(d) to its row; the queue adds I (W - 1) for the boundary
+        // points (Appendix A per-point rule).  One warp vote per column covers
+        // both rare events: a ray that FP32 cannot decide, and a boundary
+        // point to queue.
+        float* dq = (float*)(wqueue + warp * 256);
+        int dq_n = 0;
+        const int CH = sh.chunk;
+        const int nch = (NTH + CH - 1) / CH;
+        const int ntask = ((NR + 31) >> 5) * nch;
+        const float rr32 = rho32 * rho32;
+        const unsigned lt_mask = (1u << lane) - 1u;
+        auto flush_queue = [&]() {
+          __syncwarp();
+          if (lane < dq_n) {
+            const float* e_ = dq + lane * 8;
+            const float I = brightness(-e_[2]);
+            float WU;
+            const float W = boundary_weight(0, e_, __float_as_int(e_[6]), __float_as_int(e_[7]), nullptr, &WU);
+            // literal rule: I (W - 1); split-profile rule: the limb value c0f
+            // with the uniform weight, the rest with f(delta)
+            const float term = split ? e_[5] * (c0f * (WU - 1.0f) + (I - c0f) * (W - 1.0f)) : e_[5] * I * (W - 1.0f);
+            const float y = term - acc_c;
+            const float tt = acc_s + y;
+            acc_c = (tt - acc_s) - y;
+            acc_s = tt;
+          }
+          __syncwarp();
+          dq_n = 0;
+        };
+        for (;;) {
+          int task = 0;
+          if (lane == 0) task = atomicAdd(&sh.task_ctr, 1);
+          task = __shfl_sync(0xffffffffu, task, 0);
+          if (task >= ntask) break;
+          const int rbk = task / nch, chk = task - rbk * nch;
+          const int i = rbk * 32 + lane;
+          const bool rowok = i < NR;
+          const int ii = rowok ? i : NR - 1;
+          const int gi = ii / gr;
+          const float dri = ((float)(ii - gi * gr) + 0.5f - 0.5f * (float)gr) * dr32;
+          const float ri = (float)(B.r_lo + (gi * gr + 0.5 * gr) * sh.dr64) + dri;
+          const int c0 = chk * CH, c1 = min(c0 + CH, NTH);
+          // anchor of the current theta group (registers)
+          int a_grp = -1, a_next = 0, a_idx = 0;
+          cf a_ws, a_A[NL], a_K[NL];
+          float a_lo2 = 0.f, a_hi2 = 0.f;
+          const float* tpx = tabx;
+          const float* tpy = taby;
+          auto load_group = [&](int lw) {
+            const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
+            if (mgrp == a_grp) return;
+            a_grp = mgrp;
+            a_next = (mgrp + 1) * gth;
+            a_idx = gi * mth + mgrp;
+            const Anchor& an_ = anch[a_idx];
+            a_ws = an_.ws;
+#pragma unroll
+            for (int j = 0; j < NL; ++j) { a_A[j] = an_.A[j]; a_K[j] = an_.K[j]; }
+            a_lo2 = an_.lo2;
+            a_hi2 = an_.hi2;
+            tpx = tabx - mgrp * gth;
+            tpy = taby - mgrp * gth;
+          };
+          unsigned win = 0u;  // inside flags: bit k = column l - k
+          float rowacc = 0.f;
+          // squared distance of ray (i, lw) in FP32 (difference form about the
+          // group's anchor) and |U|_1 for its own error bound
+          auto ray = [&](int lw, float* uab) -> float {
+            const cf t = mk(tpx[lw], tpy[lw]);
+            const cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
+            cf U;
+            if constexpr (NL == 2) {
+              const cf Q0 = a_A[0] + dz, Q1 = a_A[1] + dz;
+              const float n0 = abs2(Q0), n1 = abs2(Q1);
+              const float ip = __fdividef(1.0f, n0 * n1);  // <= 2 ulp, inside the error bound
+              const cf t0 = a_K[0] * cj(Q0), t1 = a_K[1] * cj(Q1);
+              U = scl(scl(t0, n1) + scl(t1, n0), ip);
+            } else {
+              const cf Q0 = a_A[0] + dz, Q1 = a_A[1] + dz, Q2 = a_A[2] + dz;
+              const float n0 = abs2(Q0), n1 = abs2(Q1), n2 = abs2(Q2);
+              const float n01 = n0 * n1;
+              const float ip = __fdividef(1.0f, n01 * n2);
+              const cf t0 = a_K[0] * cj(Q0), t1 = a_K[1] * cj(Q1), t2 = a_K[2] * cj(Q2);
+              U = scl(scl(t0, n1 * n2) + scl(t1, n0 * n2) + scl(t2, n01), ip);
+            }
+            const cf pz = dz * U;
+            const cf dw = mk(a_ws.x + dz.x + pz.x, a_ws.y + dz.y - pz.y);
+            *uab = fabsf(U.x) + fabsf(U.y);
+            return abs2(dw);
+          };
+          // the ray's own bound decides; FP64 where it cannot
+          auto resolve = [&](float& d2, float uab, int lw) -> bool {
+            const Anchor& an_ = anch[a_idx];
+            const float eb = fmaf(an_.e1, uab, an_.e0);
+            if (fabsf(d2 - rr32) <= 2.0f * rho32 * eb + eb * eb) {
+              const double d64 = ray_distance64<NL>(sh, B, ii, lw);
+              if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
+              d2 = (float)(d64 * d64);
+              return d64 < sh.rho;
+            }
+            return d2 < rr32;
+          };
+          // queue boundary point m = l - 2 with its stencil (v[m-2..m+2]) =
+          // (a, b, c, d, e), the inside flags at bits 4..0 of win
+          auto push = [&](bool isb, int m, float a, float b, float c, float d, float e) {
+            const unsigned bm = __ballot_sync(0xffffffffu, isb);
+            if (!bm) return;
+            if (dq_n + __popc(bm) > 32) flush_queue();
+            if (isb) {
+              float* e_ = dq + (dq_n + __popc(bm & lt_mask)) * 8;
+              const float v5[5] = {a, b, c, d, e};
+#pragma unroll
+              for (int k = 0; k < 5; ++k)
+                e_[k] = __int_as_float(__float_as_int(v5[k]) | (((win >> (4 - k)) & 1u) << 31));
+              e_[5] = ri * bxw;
+              e_[6] = __int_as_float(m);
+              e_[7] = __int_as_float(i);
+            }
+            dq_n += __popc(bm);
+          };
+          // main column l (inside [c0, c1), no wrap; the group already
+          // loaded): ring (a, b, c, d) = v[l-4..l-1], result into dst.  The
+          // boundary test of the centre m = l - 2 needs only the flags of
+          // l - 3 .. l - 1 (bits 0..2 of win before the shift), so it shares
+          // the column's vote.
+          auto main_col = [&](int l, bool fin, float& dst, float a, float b, float c, float d) {
+            float uab;
+            float d2 = ray(l, &uab);
+            bool in = d2 < a_lo2;
+            const bool unc = !in && !(d2 > a_hi2);
+            const bool isb = fin && rowok && (win & 2u) && ((win & 5u) != 5u);
+            if (__any_sync(0xffffffffu, unc || isb)) {
+              if (unc) in = resolve(d2, uab, l);
+              win = (win << 1) | (in ? 1u : 0u);
+              push(isb, l - 2, a, b, c, d, d2);
+            } else {
+              win = (win << 1) | (in ? 1u : 0u);
+            }
+            if (in) rowacc += brightness(d2);
+            dst = d2;
+          };
+          // halo column (wrapped, or beyond a non-periodic edge)
+          auto halo = [&](int l) -> float {
+            const bool beyond = !B.periodic && (l < 0 || l >= NTH);
+            float d2 = __int_as_float(0x7f800000);
+            bool in = false;
+            if (!beyond) {
+              const int lw = wrapl(l);
+              load_group(lw);
+              float uab;
+              d2 = ray(lw, &uab);
+              in = d2 < a_lo2;
+              const bool unc = !in && !(d2 > a_hi2);
+              if (__any_sync(0xffffffffu, unc))
+                if (unc) in = resolve(d2, uab, lw);
+            }
+            win = (win << 1) | (in ? 1u : 0u);
+            return d2;
+          };
+          float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3, r4;
+          r3 = halo(c0 - 2);
+          r4 = halo(c0 - 1);
+          // main columns: ring r0..r4 holds v[l-5..l-1] before column l; the
+          // first two finalize nothing (their centres are halo columns)
+          int l = c0;
+          load_group(l);
+#pragma unroll 1
+          for (int k = 0; k < 2 && l < c1; ++k, ++l) {
+            if (l >= a_next) load_group(l);
+            float nv;
+            main_col(l, false, nv, r1, r2, r3, r4);
+            r0 = r1; r1 = r2; r2 = r3; r3 = r4; r4 = nv;
+          }
+#pragma unroll 1
+          while (l < c1) {
+            if (l >= a_next) load_group(l);
+            // columns up to the group end or the chunk end, five at a time
+            const int lend = min(a_next, c1);
+#pragma unroll 1
+            for (; l + 5 <= lend; l += 5) {
+              main_col(l + 0, true, r0, r1, r2, r3, r4);
+              main_col(l + 1, true, r1, r2, r3, r4, r0);
+              main_col(l + 2, true, r2, r3, r4, r0, r1);
+              main_col(l + 3, true, r3, r4, r0, r1, r2);
+              main_col(l + 4, true, r4, r0, r1, r2, r3);
+            }
+#pragma unroll 1
+            for (; l < lend; ++l) {
+              float nv;
+              main_col(l, true, nv, r1, r2, r3, r4);
+              r0 = r1; r1 = r2; r2 = r3; r3 = r4; r4 = nv;
+            }
+          }
+          // right halo: finalizes the last two columns of the chunk
+#pragma unroll 1
+          for (int k = 0; k < 2; ++k, ++l) {
+            const bool isb = l - 2 >= c0 && rowok && (win & 2u) && ((win & 5u) != 5u);
+            const float nv = halo(l);
+            if (__any_sync(0xffffffffu, isb)) push(isb, l - 2, r1, r2, r3, r4, nv);
+            r0 = r1; r1 = r2; r2 = r3; r3 = r4; r4 = nv;
+          }
+          if (rowok) {
+            const float term = ri * rowacc * bxw;
+            const float y = term - acc_c;
+            const float tt = acc_s + y;
+            acc_c = (tt - acc_s) - y;
+            acc_s = tt;
+          }
+        }
+        flush_queue();
+      } else {
       for (int i = warp; i < NR; i += NW) {
         const int gi = i / gr;
         const float dri = ((float)(i - gi * gr) + 0.5f - 0.5f * (float)gr) * dr32;
@@ -1553,7 +1848,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
             const int o = lw - mgrp * gth;
             const Anchor& an_ = anch[gi * mth + mgrp];
-            cf t = tab[o];
+            cf t = mk(tabx[o], taby[o]);
             cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
             cf U;
             if constexpr (NL == 2) {
@@ -1728,7 +2023,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
               const int o = lw - mgrp * gth;
               const Anchor& an_ = anch[gi * mth + mgrp];
-              const cf t = tab[o];
+              const cf t = mk(tabx[o], taby[o]);
               const cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
               const cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz;
               const float n0 = abs2(Q0), n1 = abs2(Q1);
@@ -1793,6 +2088,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         acc_s = tt;
       }
       if (DEFER) flush_deferred();
+      }  // DER row loop
       __syncthreads();
       if (DER && tid < 12) {
         double sum = 0.0;
@@ -1864,6 +2160,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
 }
 
 // ---------------------------------------------------------------- point source
+// One thread per source position: images and magnification of a point source
+// (point_source_solve, shared with the surrogate's feature kernel).
 template <int NL>
 __global__ void point_source_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ W, int n,
                                     icrs_grid g, double* __restrict__ A, double* __restrict__ images,
@@ -1871,103 +2169,83 @@ __global__ void point_source_kernel(const icrs_params* __restrict__ P, int S, co
   constexpr int N = NL * NL + 1;
   long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)S * n) return;
-  int s = (int)(idx / n);
-  Lens L = make_lens(P[s]);
-  cd w = mk(W[2 * idx], W[2 * idx + 1]);
-  const int ll = L.ll;
-  float eps32[NL];
-  cf a32[NL], D[NL + 1], E[NL];
-  double epsd[NL];
-  cd ad[NL], Dd[NL + 1], Ed[NL];
-  for (int i = 0; i < NL; ++i) { epsd[i] = L.eps[i]; ad[i] = L.a[i] - L.a[ll]; eps32[i] = (float)epsd[i]; a32[i] = tof(ad[i]); }
-  poly_DE<NL, double>(epsd, ad, Dd, Ed);
-  for (int i = 0; i <= NL; ++i) D[i] = tof(Dd[i]);
-  for (int i = 0; i < NL; ++i) E[i] = tof(Ed[i]);
-  cd wl = w - L.a[ll];
-  cf b[N + 1];
-  lens_poly<NL, float>(eps32, a32, D, E, tof(wl), b);
-  cf z[N];
-  float last[N];
-  cauchy_start<N>(b, z);
-  uint32_t st = 0;
-  if (ehrlich_aberth_f32<N>(b, z, g.max_iter, 4.0f * EPS32, last) < 0) st |= ICRS_ST_NONCONV;
-  // candidate roots in the original frame (FP64); for a triple lens the roots
-  // nearest the second light lens come from a second EA about that lens
-  cd cand[2 * N];
-  int nc = 0;
-  int l2 = -1;
-  if (NL == 3) {
-    for (int i = 0; i < NL; ++i) if (i != ll && (l2 < 0 || L.eps[i] < L.eps[l2])) l2 = i;
+  const int s = (int)(idx / n);
+  const Lens L = make_lens(P[s]);
+  const cd w = mk(W[2 * idx], W[2 * idx + 1]);
+  const PointSource<NL> r = point_source_solve<NL>(L, w, g.max_iter, g.img_tol, images ? images + idx * N * 2 : nullptr);
+  A[idx] = r.A;
+  if (n_img) n_img[idx] = r.m;
+  if (status) status[idx] = r.st;
+}
+
+// ---------------------------------------------------------------- likelihood
+// Linear-flux marginalised NLL of one light curve per block (Appendix B,
+// Eq. NLL, Woodbury form), and optionally its gradient sum_e dnll/dA_e dA_e/dp
+// from the per-epoch derivatives dA [S][E][8].  Fixed-order FP64 sums.
+constexpr int NLL_THREADS = 256;
+
+__device__ inline double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < NLL_THREADS / 32; ++w) s += red[w];
+  return s;
+}
+
+__global__ void __launch_bounds__(NLL_THREADS)
+marginal_nll_kernel(const double* __restrict__ A, const double* __restrict__ F, const double* __restrict__ sig,
+                    const double* __restrict__ prior, int E, const double* __restrict__ dA,
+                    double* __restrict__ nll, double* __restrict__ grad, double* __restrict__ fluxes) {
+  __shared__ double red[NLL_THREADS / 32];
+  const int s = blockIdx.x;
+  const size_t o = (size_t)s * E;
+  const double mu0 = prior[4 * s + 0], mu1 = prior[4 * s + 1];
+  const double l0 = prior[4 * s + 2], l1 = prior[4 * s + 3];
+  // sums over the epochs: M^T C^-1 M, M^T C^-1 r, r^T C^-1 r, ln|C|
+  // (r = F - M mu, m_e = (A_e - 1, 1), c_e = 1 / sigma_e^2)
+  double saa = 0, sa1 = 0, s11 = 0, sar = 0, s1r = 0, srr = 0, slc = 0, nbad = 0;
+  for (int e = threadIdx.x; e < E; e += NLL_THREADS) {
+    const double a = A[o + e] - 1.0, sg = sig[o + e];
+    const double c = 1.0 / (sg * sg);
+    const double r = F[o + e] - mu0 * a - mu1;
+    saa += c * a * a; sa1 += c * a; s11 += c;
+    sar += c * a * r; s1r += c * r; srr += c * r * r;
+    slc += log(sg * sg);
+    if (!(sg > 0.0)) nbad += 1.0;
   }
-  for (int j = 0; j < N; ++j) {
-    cd z0 = tod(z[j]) + L.a[ll];
-    int nj = 0;
-    double best = abs2(z0 - L.a[0]);
-    for (int i = 1; i < NL; ++i) { double d = abs2(z0 - L.a[i]); if (d < best) { best = d; nj = i; } }
-    if (NL == 3 && nj == l2) continue;
-    cand[nc++] = z0;
+  saa = block_sum(saa, red); sa1 = block_sum(sa1, red); s11 = block_sum(s11, red);
+  sar = block_sum(sar, red); s1r = block_sum(s1r, red); srr = block_sum(srr, red);
+  slc = block_sum(slc, red); nbad = block_sum(nbad, red);
+  // K = Lambda^-1 + M^T C^-1 M and its inverse
+  const double k00 = 1.0 / l0 + saa, k01 = sa1, k11 = 1.0 / l1 + s11;
+  const double det = k00 * k11 - k01 * k01;
+  const double i00 = k11 / det, i01 = -k01 / det, i11 = k00 / det;
+  const double kv0 = i00 * sar + i01 * s1r, kv1 = i01 * sar + i11 * s1r;  // K^-1 v
+  const double a0 = mu0 + kv0, a1 = mu1 + kv1;                              // posterior mean
+  const bool bad = nbad > 0.0 || !(l0 > 0.0) || !(l1 > 0.0) || !(det > 0.0);
+  if (threadIdx.x == 0) {
+    const double quad = srr - (sar * kv0 + s1r * kv1);
+    const double logdet = slc + log(l0) + log(l1) + log(det);
+    nll[s] = bad ? __longlong_as_double(0x7ff8000000000000LL) : 0.5 * (quad + logdet);
+    if (fluxes) { fluxes[2 * s] = a0; fluxes[2 * s + 1] = a1; }
   }
-  if (NL == 3) {
-    cd a2[NL], D2d[NL + 1], E2d[NL];
-    cf a2f[NL], D2[NL + 1], E2[NL], b2[N + 1], z2[N];
-    for (int i = 0; i < NL; ++i) { a2[i] = L.a[i] - L.a[l2]; a2f[i] = tof(a2[i]); }
-    poly_DE<NL, double>(epsd, a2, D2d, E2d);
-    for (int i = 0; i <= NL; ++i) D2[i] = tof(D2d[i]);
-    for (int i = 0; i < NL; ++i) E2[i] = tof(E2d[i]);
-    lens_poly<NL, float>(eps32, a2f, D2, E2, tof(w - L.a[l2]), b2);
-    for (int j = 0; j < N; ++j) z2[j] = tof(tod(z[j]) + L.a[ll] - L.a[l2]);
-    if (ehrlich_aberth_f32<N>(b2, z2, g.max_iter, 4.0f * EPS32, last) < 0) st |= ICRS_ST_NONCONV;
-    for (int j = 0; j < N; ++j) {
-      cd z0 = tod(z2[j]) + L.a[l2];
-      int nj = 0;
-      double best = abs2(z0 - L.a[0]);
-      for (int i = 1; i < NL; ++i) { double d = abs2(z0 - L.a[i]); if (d < best) { best = d; nj = i; } }
-      if (nj != l2) continue;
-      if (nc < 2 * N) cand[nc++] = z0;
-    }
+  if (!grad) return;
+  double gq[NPAR];
+  for (int q = 0; q < NPAR; ++q) gq[q] = 0.0;
+  for (int e = threadIdx.x; e < E; e += NLL_THREADS) {
+    const double a = A[o + e] - 1.0, sg = sig[o + e];
+    const double c = 1.0 / (sg * sg);
+    const double ge = c * ((i00 * a + i01) - (F[o + e] - a * a0 - a1) * a0);
+    const double* d = dA + (o + e) * NPAR;
+    for (int q = 0; q < NPAR; ++q) gq[q] += ge * d[q];
   }
-  // FP64 polish on the polynomial about each root's nearest lens, then
-  // validation against img_tol (the same as the sector path's FP64 checks).
-  double Asum = 0.0;
-  int m = 0;
-  for (int j = 0; j < nc; ++j) {
-    cd z0 = cand[j];
-    int nj = 0;
-    double best = abs2(z0 - L.a[0]);
-    for (int i = 1; i < NL; ++i) { double d = abs2(z0 - L.a[i]); if (d < best) { best = d; nj = i; } }
-    cd aj[NL], Dj[NL + 1], Ej[NL], bj[N + 1];
-    for (int i = 0; i < NL; ++i) aj[i] = L.a[i] - L.a[nj];
-    poly_DE<NL, double>(epsd, aj, Dj, Ej);
-    cd wj = w - L.a[nj];
-    lens_poly<NL, double>(epsd, aj, Dj, Ej, wj, bj);
-    cd x = z0 - L.a[nj];
-    for (int it = 0; it < 8; ++it) {
-      cd p, dp;
-      horner2<N, double>(bj, x, p, dp);
-      if (!(abs2(dp) > 0.0)) break;
-      cd stp = dv(p, dp);
-      x = x - stp;
-      if (abs2(stp) <= 1e-30 * fmax(1.0, abs2(x))) break;
-    }
-    cd F = lens_map<NL, double>(epsd, aj, x) - wj;
-    if (!(sqrt(abs2(F)) <= g.img_tol)) continue;
-    if (m >= N) { st |= ICRS_ST_OVERFLOW; break; }
-    cd gm = shear<NL, double>(epsd, aj, x);
-    Asum += 1.0 / fabs(1.0 - abs2(gm));
-    if (images) {
-      cd zz = x + L.a[nj];
-      images[(idx * N + m) * 2] = zz.x;
-      images[(idx * N + m) * 2 + 1] = zz.y;
-    }
-    ++m;
+  for (int q = 0; q < NPAR; ++q) {
+    const double v = block_sum(gq[q], red);
+    if (threadIdx.x == 0) grad[(size_t)s * NPAR + q] = v;
   }
-  bool legal = (NL == 2) ? (m == 3 || m == 5) : (m == 4 || m == 6 || m == 8 || m == 10);
-  if (!legal) st |= ICRS_ST_IMGCOUNT;
-  if (images)
-    for (int j = m; j < N; ++j) { images[(idx * N + j) * 2] = 0.0; images[(idx * N + j) * 2 + 1] = 0.0; }
-  A[idx] = Asum;
-  if (n_img) n_img[idx] = m;
-  if (status) status[idx] = st;
 }
 
 // ---------------------------------------------------------------- host side
@@ -1980,11 +2258,11 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += 3 * ((NP + 15) & ~(size_t)15);
   b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
   const int NW = nt / 32;
-  b += sizeof(int) * NW * ((!der && NL == 2 && defer) ? 256 : 64);  // per-warp boundary queues
+  (void)defer;
+  b += sizeof(int) * NW * (!der ? 256 : 64);  // per-warp boundary queues
   const int seg = row_segment(g.n_theta, der);
-  if (der) b += sizeof(DerShared) + sizeof(float) * NW * (seg + 4);  // state and ray seeds
-  b += sizeof(cf) * g.n_theta;
-  b += sizeof(float) * NW * (seg + 4);
+  if (der) b += sizeof(DerShared) + 2 * sizeof(float) * NW * (seg + 4);  // state, row buffers and ray seeds
+  b += sizeof(cf) * (GTH_MAX + 2);
   b += sizeof(cdf) * g.n_limb;
   return b;
 }
@@ -1998,6 +2276,7 @@ static int check_grid(const icrs_grid* g) {
   if (g->n_bins_theta < 2 || g->n_bins_theta > 64) return ICRS_EINVAL;
   if (!(g->delta_c > 0.0) || !(g->margin >= 0.0) || !(g->img_tol > 0.0)) return ICRS_EINVAL;
   if (g->max_iter < 1 || g->max_iter > 10000) return ICRS_EINVAL;
+  if (g->ld_split != 0 && g->ld_split != 1) return ICRS_EINVAL;
   return ICRS_OK;
 }
 
@@ -2116,7 +2395,7 @@ static int launch_der(const icrs_params* p, int S, const double* t, int E, const
   if (!p || !t) return ICRS_EINVAL;
   int nl = g->n_lens;
   if (nl == 0) { rc = first_n_lens(p, st, &nl); if (rc) return rc; }
-  if (nl == 3) return ICRS_EUNSUPPORTED;
+  if (nl == 3 || g->ld_split) return ICRS_EUNSUPPORTED;
   if (nl != 2) return ICRS_EINVAL;
   return launch_inst<2, true>(p, S, t, E, g, A, status, nullptr, nullptr, nullptr, d, st);
 }
@@ -2127,7 +2406,7 @@ using namespace icrs;
 
 extern "C" {
 
-int icrs_abi_version(void) { return 1; }
+int icrs_abi_version(void) { return 2; }
 
 void icrs_grid_default(icrs_grid* g) {
   if (!g) return;
@@ -2178,6 +2457,37 @@ int icrs_magnification_diag(const icrs_params* p, int S, const double* t, int E,
                             double* A, uint32_t* status, double* sectors, int32_t* counters,
                             float* points, void* stream) {
   return launch_mag(p, S, t, E, g, A, status, sectors, counters, points, stream);
+}
+
+size_t icrs_marginal_nll_workspace_bytes(int S, int E) {
+  if (S <= 0 || E <= 0) return 0;
+  return sizeof(double) * (size_t)S * (size_t)E * (NPAR + 1);
+}
+
+int icrs_marginal_nll_grad(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, const double* F,
+                           const double* sigma, const double* prior, double* nll, double* grad, double* fluxes,
+                           double* A, uint32_t* status, void* workspace, size_t workspace_bytes, void* stream) {
+  if (S < 0 || E < 0) return ICRS_EINVAL;
+  int rc = check_grid(g);
+  if (rc) return rc;
+  if (S == 0) return ICRS_OK;
+  if (!p || !prior || !nll || (E > 0 && (!t || !F || !sigma))) return ICRS_EINVAL;
+  const size_t need = icrs_marginal_nll_workspace_bytes(S, E);
+  if (E > 0 && (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 7u))) return ICRS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* dA = (double*)workspace;
+  double* Aw = A ? A : (E > 0 ? dA + (size_t)S * E * NPAR : nullptr);
+  if (E > 0) {
+    if (grad) {
+      DerOut d = {nullptr, nullptr, nullptr, dA, nullptr, nullptr};
+      rc = launch_der(p, S, t, E, g, d, Aw, status, stream);
+    } else {
+      rc = launch_mag(p, S, t, E, g, Aw, status, nullptr, nullptr, nullptr, stream);
+    }
+    if (rc) return rc;
+  }
+  marginal_nll_kernel<<<S, NLL_THREADS, 0, st>>>(Aw, F, sigma, prior, E, dA, nll, grad, fluxes);
+  return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
 }
 
 int icrs_magnification_indexed(const icrs_params* p, int S, const double* t, int E, const int32_t* items, int n,

@@ -1,7 +1,7 @@
 // Point-source images and magnification at one source position (Sec. 2.1:
 // Eqs. lens_eq, amp_point, detJ; roots by Ehrlich-Aberth, Sec. 3.1), one
-// thread per position, for the surrogate's feature kernel.  The steps are
-// those of icrs_point_source's kernel.
+// thread per position.  Used by icrs_point_source's kernel and by the
+// surrogate's feature kernel.
 #pragma once
 
 #include "icrs_common.cuh"
@@ -16,18 +16,62 @@ struct PointSource {
   uint32_t st;     // ICRS_ST_* bits
 };
 
-// FP32 Ehrlich-Aberth on the polynomial about the lightest lens (triple: a
-// second one about the second-lightest lens for the roots nearest it), then
-// FP64 Newton on the polynomial about each root's nearest lens and validation
-// against img_tol in that frame.  images (optional): [N_deg][2] positions,
-// the first m valid, the rest zero.
+// Index of the lens nearest to z (original frame).
 template <int NL>
-__device__ __forceinline__ PointSource<NL> point_source_solve(const Lens L, const cd w, const int max_iter,
-                                                              const double img_tol, double* images) {
-  // binary only (the feature kernel's case).  Everything is passed by value:
-  // an earlier form that took the lens and the grid (a kernel parameter) by
-  // reference returned wrong image counts on the GPU.
-  static_assert(NL == 2, "point_source_solve is validated for binary lenses only");
+__device__ __forceinline__ int ps_nearest_lens(const Lens& L, cd z) {
+  int nj = 0;
+  double best = abs2(z - L.a[0]);
+  for (int i = 1; i < NL; ++i) { double d = abs2(z - L.a[i]); if (d < best) { best = d; nj = i; } }
+  return nj;
+}
+
+// FP64 Newton on the polynomial about the nearest lens of z0, then the
+// lens-equation residual in that frame against img_tol.  Returns 1 and the
+// polished image (original frame) and |det J| if z0 converges to an image.
+// *conv is cleared when the Newton steps had not converged (linear
+// convergence next to a near-double root, where an iterate can still pass
+// the residual test).
+template <int NL>
+__device__ inline int ps_polish_validate(const Lens& L, const double* epsd, cd w, cd z0, double img_tol, cd* zi,
+                                         double* det, int* conv) {
+  constexpr int N = NL * NL + 1;
+  const int nj = ps_nearest_lens<NL>(L, z0);
+  cd aj[NL], Dj[NL + 1], Ej[NL], bj[N + 1];
+  for (int i = 0; i < NL; ++i) aj[i] = L.a[i] - L.a[nj];
+  poly_DE<NL, double>(epsd, aj, Dj, Ej);
+  const cd wj = w - L.a[nj];
+  lens_poly<NL, double>(epsd, aj, Dj, Ej, wj, bj);
+  cd x = z0 - L.a[nj];
+  *conv = 0;
+  for (int it = 0; it < 8; ++it) {
+    cd p, dp;
+    horner2<N, double>(bj, x, p, dp);
+    if (!(abs2(dp) > 0.0)) break;
+    const cd stp = dv(p, dp);
+    x = x - stp;
+    if (abs2(stp) <= 1e-30 * fmax(1.0, abs2(x))) { *conv = 1; break; }
+  }
+  const cd F = lens_map<NL, double>(epsd, aj, x) - wj;
+  if (!(sqrt(abs2(F)) <= img_tol)) return 0;
+  const cd gm = shear<NL, double>(epsd, aj, x);
+  *det = fabs(1.0 - abs2(gm));
+  *zi = x + L.a[nj];
+  return 1;
+}
+
+// Images of the source position w.  FP32 Ehrlich-Aberth on the polynomial
+// about the lightest lens (triple: a second one about the second-lightest
+// lens for the roots nearest it), then FP64 Newton on the polynomial about
+// each root's nearest lens and validation against img_tol in that frame.  If
+// that image set is not trustworthy (an illegal count, a Newton polish that
+// did not converge, or two roots that polish to the same image: FP32
+// approximations that met at one root of a close cluster), all roots are
+// solved again by FP64 Ehrlich-Aberth from the FP32 ones (their converged
+// roots validated the same way).  images (optional): [N_deg][2]
+// positions, the first m valid, the rest zero.
+template <int NL>
+__device__ inline PointSource<NL> point_source_solve(const Lens L, const cd w, const int max_iter,
+                                                     const double img_tol, double* images) {
   constexpr int N = NL * NL + 1;
   constexpr float kEps32 = 5.9604645e-8f;
   const int ll = L.ll;
@@ -39,7 +83,7 @@ __device__ __forceinline__ PointSource<NL> point_source_solve(const Lens L, cons
   poly_DE<NL, double>(epsd, ad, Dd, Ed);
   for (int i = 0; i <= NL; ++i) D[i] = tof(Dd[i]);
   for (int i = 0; i < NL; ++i) E[i] = tof(Ed[i]);
-  cd wl = w - L.a[ll];
+  const cd wl = w - L.a[ll];
   cf b[N + 1];
   lens_poly<NL, float>(eps32, a32, D, E, tof(wl), b);
   cf z[N];
@@ -56,11 +100,8 @@ __device__ __forceinline__ PointSource<NL> point_source_solve(const Lens L, cons
     for (int i = 0; i < NL; ++i) if (i != ll && (l2 < 0 || L.eps[i] < L.eps[l2])) l2 = i;
   }
   for (int j = 0; j < N; ++j) {
-    cd z0 = tod(z[j]) + L.a[ll];
-    int nj = 0;
-    double best = abs2(z0 - L.a[0]);
-    for (int i = 1; i < NL; ++i) { double d = abs2(z0 - L.a[i]); if (d < best) { best = d; nj = i; } }
-    if (NL == 3 && nj == l2) continue;
+    const cd z0 = tod(z[j]) + L.a[ll];
+    if (NL == 3 && ps_nearest_lens<NL>(L, z0) == l2) continue;
     cand[nc++] = z0;
   }
   if (NL == 3) {
@@ -74,51 +115,57 @@ __device__ __forceinline__ PointSource<NL> point_source_solve(const Lens L, cons
     for (int j = 0; j < N; ++j) z2[j] = tof(tod(z[j]) + L.a[ll] - L.a[l2]);
     if (ehrlich_aberth_f32<N>(b2, z2, max_iter, 4.0f * kEps32, last) < 0) out.st |= ICRS_ST_NONCONV;
     for (int j = 0; j < N; ++j) {
-      cd z0 = tod(z2[j]) + L.a[l2];
-      int nj = 0;
-      double best = abs2(z0 - L.a[0]);
-      for (int i = 1; i < NL; ++i) { double d = abs2(z0 - L.a[i]); if (d < best) { best = d; nj = i; } }
-      if (nj != l2) continue;
+      const cd z0 = tod(z2[j]) + L.a[l2];
+      if (ps_nearest_lens<NL>(L, z0) != l2) continue;
       if (nc < 2 * N) cand[nc++] = z0;
     }
   }
-  double Asum = 0.0, mind = __longlong_as_double(0x7ff0000000000000LL);
+  cd img[N];
+  double dets[N];
   int m = 0;
+  bool trust = true;
   for (int j = 0; j < nc; ++j) {
-    cd z0 = cand[j];
-    int nj = 0;
-    double best = abs2(z0 - L.a[0]);
-    for (int i = 1; i < NL; ++i) { double d = abs2(z0 - L.a[i]); if (d < best) { best = d; nj = i; } }
-    cd aj[NL], Dj[NL + 1], Ej[NL], bj[N + 1];
-    for (int i = 0; i < NL; ++i) aj[i] = L.a[i] - L.a[nj];
-    poly_DE<NL, double>(epsd, aj, Dj, Ej);
-    cd wj = w - L.a[nj];
-    lens_poly<NL, double>(epsd, aj, Dj, Ej, wj, bj);
-    cd x = z0 - L.a[nj];
-    for (int it = 0; it < 8; ++it) {
-      cd p, dp;
-      horner2<N, double>(bj, x, p, dp);
-      if (!(abs2(dp) > 0.0)) break;
-      cd stp = dv(p, dp);
-      x = x - stp;
-      if (abs2(stp) <= 1e-30 * fmax(1.0, abs2(x))) break;
-    }
-    cd F = lens_map<NL, double>(epsd, aj, x) - wj;
-    if (!(sqrt(abs2(F)) <= img_tol)) continue;
-    if (m >= N) { out.st |= ICRS_ST_OVERFLOW; break; }
-    cd gm = shear<NL, double>(epsd, aj, x);
-    double det = fabs(1.0 - abs2(gm));
-    Asum += 1.0 / det;
-    mind = fmin(mind, det);
-    if (images) {
-      cd zz = x + L.a[nj];
-      images[m * 2] = zz.x;
-      images[m * 2 + 1] = zz.y;
-    }
+    cd zi;
+    double det;
+    int conv;
+    if (!ps_polish_validate<NL>(L, epsd, w, cand[j], img_tol, &zi, &det, &conv)) continue;
+    if (!conv) trust = false;
+    for (int i = 0; i < m; ++i)
+      if (abs2(zi - img[i]) <= 1e-18 * fmax(1.0, abs2(zi))) trust = false;
+    if (m >= N) { trust = false; break; }
+    img[m] = zi;
+    dets[m] = det;
     ++m;
   }
-  bool legal = (NL == 2) ? (m == 3 || m == 5) : (m == 4 || m == 6 || m == 8 || m == 10);
-  if (!legal) out.st |= ICRS_ST_IMGCOUNT;
+  auto legal = [](int c) { return (NL == 2) ? (c == 3 || c == 5) : (c == 4 || c == 6 || c == 8 || c == 10); };
+  if (!trust || !legal(m)) {
+    // FP64 Ehrlich-Aberth on all roots (polynomial about the lightest lens),
+    // warm-started from the FP32 roots, then the same polish and validation
+    cd bd[N + 1], zd[N];
+    lens_poly<NL, double>(epsd, ad, Dd, Ed, wl, bd);
+    for (int j = 0; j < N; ++j) zd[j] = tod(z[j]);
+    for (int j = 1; j < N; ++j)
+      for (int i = 0; i < j; ++i)
+        if (abs2(zd[j] - zd[i]) < 1e-20) zd[j] = zd[j] + mk(1e-7 * (j + 1), 1e-7 * j);
+    if (ehrlich_aberth_f64<N>(bd, zd, max_iter) < 0) out.st |= ICRS_ST_NONCONV;
+    m = 0;
+    for (int j = 0; j < N; ++j) {
+      cd zi;
+      double det;
+      int conv;
+      if (!ps_polish_validate<NL>(L, epsd, w, zd[j] + L.a[ll], img_tol, &zi, &det, &conv)) continue;
+      img[m] = zi;
+      dets[m] = det;
+      ++m;
+    }
+  }
+  if (!legal(m)) out.st |= ICRS_ST_IMGCOUNT;
+  double Asum = 0.0, mind = __longlong_as_double(0x7ff0000000000000LL);
+  for (int j = 0; j < m; ++j) {
+    Asum += 1.0 / dets[j];
+    mind = fmin(mind, dets[j]);
+    if (images) { images[j * 2] = img[j].x; images[j * 2 + 1] = img[j].y; }
+  }
   if (images)
     for (int j = m; j < N; ++j) { images[j * 2] = 0.0; images[j * 2 + 1] = 0.0; }
   out.A = Asum;

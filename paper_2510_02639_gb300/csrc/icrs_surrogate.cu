@@ -610,6 +610,72 @@ __global__ void gate_scatter_kernel(const uint8_t* __restrict__ flag, int n, con
   if (f) routed_idx[off + __popc(b & ((1u << lanei) - 1u))] = q;
 }
 
+// ---------------------------------------------------------------- epoch preselection
+// Non-learned gate (Sec. 3.4 (iii): the extended-source computation runs only
+// on a preselected set of epochs near caustics).  An epoch is near a caustic
+// unless its point-source solves are clean (status 0), its caustic feature is
+// at least caustic_min, the second-order finite-source estimate |b| is at most
+// b_max and A_ps is at most A_max (A_small for rho < rho_min).  Every epoch of
+// the same light curve within n_ext epochs of a near-caustic one is routed
+// too.  The rest get the estimate: A_ps (mode 0) or A_ps exp(1e-4 b) (mode 1).
+__global__ void epoch_near_kernel(const float* __restrict__ feat, const double* __restrict__ A_ps,
+                                  const uint32_t* __restrict__ st_ps, int n, float b_max, float caustic_min,
+                                  double A_max, float rho_min, double A_small, uint8_t* __restrict__ near) {
+  const int q = blockIdx.x * GB + threadIdx.x;
+  if (q >= n) return;
+  const float base = feat[(size_t)q * 8 + 7];
+  const bool ok = st_ps[q] == 0u && feat[(size_t)q * 8 + 6] >= caustic_min && fabsf(base) <= b_max &&
+                  A_ps[q] <= (feat[(size_t)q * 8 + 4] >= log10f(rho_min) + 3.0f ? A_max : A_small);
+  near[q] = ok ? 0 : 1;
+}
+
+__global__ void epoch_extend_kernel(const uint8_t* __restrict__ near, const float* __restrict__ feat,
+                                    const double* __restrict__ A_ps, int S, int E, int n_ext, int mode,
+                                    double* __restrict__ A, uint8_t* __restrict__ flag,
+                                    int32_t* __restrict__ bcount) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const long long n = (long long)S * E;
+  const long long q = (long long)blockIdx.x * GB + threadIdx.x;
+  int routed = 0;
+  if (q < n) {
+    const int e = (int)(q % E);
+    const long long row = q - e;
+    const int e0 = e - n_ext < 0 ? 0 : e - n_ext;
+    const int e1 = e + n_ext >= E ? E - 1 : e + n_ext;
+    for (int k = e0; k <= e1 && !routed; ++k) routed = near[row + k];
+    if (!routed)
+      A[q] = mode == 0 ? A_ps[q] : A_ps[q] * exp((double)feat[(size_t)q * 8 + 7] / (double)TARGET_SCALE);
+    flag[q] = (uint8_t)routed;
+  }
+  const unsigned b = __ballot_sync(0xffffffffu, routed);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(&cnt, __popc(b));
+  __syncthreads();
+  if (threadIdx.x == 0) bcount[blockIdx.x] = cnt;
+}
+
+// ---------------------------------------------------------------- training data
+// Target of the network: y = 1e4 log(A_ICRS / A_ps) - b (b = features[7]).
+__global__ void target_kernel(const double* __restrict__ A, const double* __restrict__ A_ps,
+                              const float* __restrict__ feat, int n, float* __restrict__ target) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  target[q] = (float)((double)TARGET_SCALE * log(A[q] / A_ps[q]) - (double)feat[(size_t)q * 8 + 7]);
+}
+
+// Mini-batch gather: rows idx[i] of (features, target).
+__global__ void batch_kernel(const float4* __restrict__ feat, const float* __restrict__ target,
+                             const int32_t* __restrict__ idx, int n, float4* __restrict__ out_feat,
+                             float* __restrict__ out_target) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const size_t r = (size_t)idx[i];
+  out_feat[2 * (size_t)i] = feat[2 * r];
+  out_feat[2 * (size_t)i + 1] = feat[2 * r + 1];
+  out_target[i] = target[r];
+}
+
 // ---------------------------------------------------------------- static scratch
 // Scratch of the allocation-free training step.  Some callers cannot ask for
 // device memory at the point where they train:
@@ -754,6 +820,53 @@ int icrs_surrogate_gate(const float* pred, const float* feat, const double* A_ps
   int32_t* bcount = (int32_t*)((uint8_t*)workspace + ((size_t)n + 255) / 256 * 256);
   gate_flags_kernel<<<nb, GB, 0, st>>>(pred, feat, A_ps, st_ps, n, sigma_max, mu_max, b_max, caustic_min, A_max,
                                        rho_min, A_small, A, flag, bcount);
+  gate_scan_kernel<<<1, 1024, 0, st>>>(bcount, nb, n_routed);
+  gate_scatter_kernel<<<nb, GB, 0, st>>>(flag, n, bcount, routed_idx);
+  return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
+}
+
+int icrs_surrogate_target(const double* A, const double* A_ps, const float* feat, int n, float* target,
+                          void* stream) {
+  if (n < 0) return ICRS_EINVAL;
+  if (n == 0) return ICRS_OK;
+  if (!A || !A_ps || !feat || !target) return ICRS_EINVAL;
+  target_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(A, A_ps, feat, n, target);
+  return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
+}
+
+int icrs_surrogate_batch(const float* feat, const float* target, const int32_t* idx, int n, float* out_feat,
+                         float* out_target, void* stream) {
+  if (n < 0) return ICRS_EINVAL;
+  if (n == 0) return ICRS_OK;
+  if (!feat || !target || !idx || !out_feat || !out_target) return ICRS_EINVAL;
+  if (((uintptr_t)feat & 15) || ((uintptr_t)out_feat & 15)) return ICRS_EINVAL;
+  batch_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>((const float4*)feat, target, idx, n,
+                                                                 (float4*)out_feat, out_target);
+  return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
+}
+
+size_t icrs_epoch_gate_workspace_bytes(int S, int E) {
+  if (S <= 0 || E <= 0) return 0;
+  const size_t n = (size_t)S * (size_t)E;
+  return (n + 255) / 256 * 256 + icrs_surrogate_gate_workspace_bytes((int)n);
+}
+
+int icrs_epoch_gate(const float* feat, const double* A_ps, const uint32_t* st_ps, int S, int E, int n_ext, int mode,
+                    float b_max, float caustic_min, double A_max, float rho_min, double A_small, double* A,
+                    int32_t* routed_idx, int32_t* n_routed, void* workspace, size_t workspace_bytes, void* stream) {
+  if (S < 0 || E < 0 || n_ext < 0 || (mode != 0 && mode != 1)) return ICRS_EINVAL;
+  if ((long long)S * E > 2147483647LL) return ICRS_EUNSUPPORTED;
+  const int n = S * E;
+  if (n == 0) return ICRS_OK;
+  if (!feat || !A_ps || !st_ps || !A || !routed_idx || !n_routed || !workspace) return ICRS_EINVAL;
+  if (workspace_bytes < icrs_epoch_gate_workspace_bytes(S, E)) return ICRS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = (n + GB - 1) / GB;
+  uint8_t* near = (uint8_t*)workspace;
+  uint8_t* flag = near + ((size_t)n + 255) / 256 * 256;
+  int32_t* bcount = (int32_t*)(flag + ((size_t)n + 255) / 256 * 256);
+  epoch_near_kernel<<<nb, GB, 0, st>>>(feat, A_ps, st_ps, n, b_max, caustic_min, A_max, rho_min, A_small, near);
+  epoch_extend_kernel<<<nb, GB, 0, st>>>(near, feat, A_ps, S, E, n_ext, mode, A, flag, bcount);
   gate_scan_kernel<<<1, 1024, 0, st>>>(bcount, nb, n_routed);
   gate_scatter_kernel<<<nb, GB, 0, st>>>(flag, n, bcount, routed_idx);
   return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;

@@ -25,6 +25,9 @@ EXPORTED = ("icrs_grid_default", "icrs_point_source", "icrs_magnification",
             "icrs_mlp_workspace_bytes", "icrs_mlp_train_step", "icrs_mlp_train_step_noalloc",
             "icrs_surrogate_features",
             "icrs_surrogate_gate_workspace_bytes", "icrs_surrogate_gate",
+            "icrs_marginal_nll_workspace_bytes", "icrs_marginal_nll_grad",
+            "icrs_surrogate_target", "icrs_surrogate_batch",
+            "icrs_epoch_gate_workspace_bytes", "icrs_epoch_gate",
             "icrs_strerror", "icrs_abi_version")
 
 MLP_NPARAM = 50818
@@ -42,20 +45,21 @@ class IcrsParams(ctypes.Structure):
                 ("n_lens", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("s", ctypes.c_double), ("q", ctypes.c_double),
                 ("q2", ctypes.c_double), ("q3", ctypes.c_double), ("s2", ctypes.c_double),
-                ("s3", ctypes.c_double), ("psi", ctypes.c_double)]
+                ("s3", ctypes.c_double), ("psi", ctypes.c_double), ("u2", ctypes.c_double)]
 
 
 class IcrsGrid(ctypes.Structure):
     _fields_ = [("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32), ("n_limb", ctypes.c_int32),
                 ("n_bins_r", ctypes.c_int32), ("n_bins_theta", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("uniform", ctypes.c_int32), ("n_lens", ctypes.c_int32),
-                ("delta_c", ctypes.c_double), ("margin", ctypes.c_double), ("img_tol", ctypes.c_double)]
+                ("delta_c", ctypes.c_double), ("margin", ctypes.c_double), ("img_tol", ctypes.c_double),
+                ("ld_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 PARAMS_DTYPE = np.dtype([("t0", "<f8"), ("tE", "<f8"), ("u0", "<f8"), ("alpha", "<f8"),
                          ("rho", "<f8"), ("u1", "<f8"), ("n_lens", "<i4"), ("reserved", "<i4"),
                          ("s", "<f8"), ("q", "<f8"), ("q2", "<f8"), ("q3", "<f8"),
-                         ("s2", "<f8"), ("s3", "<f8"), ("psi", "<f8")])
+                         ("s2", "<f8"), ("s3", "<f8"), ("psi", "<f8"), ("u2", "<f8")])
 assert PARAMS_DTYPE.itemsize == ctypes.sizeof(IcrsParams)
 
 
@@ -86,6 +90,11 @@ def _load():
     L.icrs_chi2_grad.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid),
                                  vp, vp, vp, vp, vp, vp, vp]
     L.icrs_chi2_grad.restype = ctypes.c_int
+    L.icrs_marginal_nll_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.icrs_marginal_nll_workspace_bytes.restype = ctypes.c_size_t
+    L.icrs_marginal_nll_grad.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(IcrsGrid),
+                                         vp, vp, vp, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.icrs_marginal_nll_grad.restype = ctypes.c_int
     L.icrs_magnification_indexed.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int,
                                              ctypes.POINTER(IcrsGrid), vp, vp, vp]
     L.icrs_magnification_indexed.restype = ctypes.c_int
@@ -109,6 +118,16 @@ def _load():
                                       ctypes.c_float, ctypes.c_double, ctypes.c_float, ctypes.c_double, vp, vp, vp, vp,
                                       ctypes.c_size_t, vp]
     L.icrs_surrogate_gate.restype = ctypes.c_int
+    L.icrs_surrogate_target.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp]
+    L.icrs_surrogate_target.restype = ctypes.c_int
+    L.icrs_surrogate_batch.argtypes = [vp, vp, vp, ctypes.c_int, vp, vp, vp]
+    L.icrs_surrogate_batch.restype = ctypes.c_int
+    L.icrs_epoch_gate_workspace_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.icrs_epoch_gate_workspace_bytes.restype = ctypes.c_size_t
+    L.icrs_epoch_gate.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_float, ctypes.c_float, ctypes.c_double, ctypes.c_float, ctypes.c_double,
+                                  vp, vp, vp, vp, ctypes.c_size_t, vp]
+    L.icrs_epoch_gate.restype = ctypes.c_int
     L.icrs_strerror.argtypes = [ctypes.c_int]
     L.icrs_strerror.restype = ctypes.c_char_p
     L.icrs_abi_version.restype = ctypes.c_int
@@ -212,7 +231,7 @@ def grid_from_dict(d: dict, n_lens: int = 2) -> IcrsGrid:
                      n_bins_r=int(d["n_bins_r"]), n_bins_theta=int(d["n_bins_theta"]),
                      max_iter=int(d["max_iter"]), uniform=int(d["uniform"]), n_lens=int(n_lens),
                      delta_c=float(d["delta_c"]), margin=float(d["margin"]),
-                     img_tol=float(d["img_tol"]))
+                     img_tol=float(d["img_tol"]), ld_split=int(d.get("ld_split", 0)))
 
 
 def magnification_vjp(params_dev, t, grid: IcrsGrid, gA, per_epoch=False, stream=None):
@@ -249,6 +268,31 @@ def chi2_grad(params_dev, t, grid: IcrsGrid, y, sigma, stream=None):
     check(lib.icrs_chi2_grad(_ptr(params_dev), S, _ptr(t), E, ctypes.byref(grid), _ptr(y), _ptr(sigma),
                              _ptr(chi2), _ptr(grad), _ptr(A), _ptr(st), _stream(torch, stream)))
     return chi2, grad, A, st
+
+
+def marginal_nll_grad(params_dev, t, grid: IcrsGrid, F, sigma, prior, grad=True, workspace=None, stream=None):
+    """Linear-flux marginalised NLL per light curve (icrs_marginal_nll_grad).
+    F, sigma: [S, E] float64; prior: [S, 4] float64 (mu_S, mu_base,
+    lambda_S, lambda_base).  Returns (nll [S], grad [S, 8] or None,
+    fluxes [S, 2], A [S, E], status [S, E])."""
+    import torch
+    S = params_dev.numel() // PARAMS_DTYPE.itemsize
+    E = t.shape[-1]
+    for x in (t, F, sigma):
+        assert x.dtype == torch.float64 and x.is_cuda and x.is_contiguous() and tuple(x.shape) == (S, E)
+    assert prior.dtype == torch.float64 and prior.is_contiguous() and tuple(prior.shape) == (S, 4)
+    nll = torch.empty((S,), dtype=torch.float64, device=t.device)
+    g = torch.empty((S, 8), dtype=torch.float64, device=t.device) if grad else None
+    fl = torch.empty((S, 2), dtype=torch.float64, device=t.device)
+    A = torch.empty((S, E), dtype=torch.float64, device=t.device)
+    st = torch.empty((S, E), dtype=torch.int32, device=t.device)
+    nb = int(lib.icrs_marginal_nll_workspace_bytes(S, E))
+    if workspace is None or workspace.numel() < nb:
+        workspace = torch.empty(max(nb, 8), dtype=torch.uint8, device=t.device)
+    check(lib.icrs_marginal_nll_grad(_ptr(params_dev), S, _ptr(t), E, ctypes.byref(grid), _ptr(F), _ptr(sigma),
+                                     _ptr(prior), _ptr(nll), _ptr(g), _ptr(fl), _ptr(A), _ptr(st), _ptr(workspace),
+                                     nb, _stream(torch, stream)))
+    return nll, g, fl, A, st
 
 
 def pack_binary(theta):
@@ -399,3 +443,47 @@ def mlp_train_step_noalloc(theta, m, v, pack, step, lr, feat, target, grad=None,
                                           _ptr(feat), _ptr(target), n, _ptr(grad), _ptr(loss), _ptr(err),
                                           _stream(torch, stream)))
     return grad, loss
+
+
+def epoch_gate(feat, A_ps, st_ps, S, E, n_ext, mode, b_max, caustic_min, A_max=1e300, rho_min=0.0, A_small=1e300,
+               A=None, stream=None):
+    """Non-learned epoch preselection (icrs_epoch_gate).  feat [S*E, 8],
+    A_ps [S*E], st_ps [S*E] from surrogate_features.  Returns (A [S*E] with
+    the non-routed epochs filled, routed_idx [S*E] int32, n_routed [1])."""
+    import torch
+    n = S * E
+    dev = feat.device
+    if A is None:
+        A = torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    idx = torch.empty((max(n, 1),), dtype=torch.int32, device=dev)
+    nr = torch.zeros((1,), dtype=torch.int32, device=dev)
+    ws = torch.empty(max(int(lib.icrs_epoch_gate_workspace_bytes(S, E)), 256), dtype=torch.uint8, device=dev)
+    check(lib.icrs_epoch_gate(_ptr(feat), _ptr(A_ps), _ptr(st_ps), int(S), int(E), int(n_ext), int(mode),
+                              float(b_max), float(caustic_min), float(A_max), float(rho_min), float(A_small),
+                              _ptr(A), _ptr(idx), _ptr(nr), _ptr(ws), ws.numel(), _stream(torch, stream)))
+    return A, idx, nr
+
+
+def surrogate_target(A, A_ps, feat, out=None, stream=None):
+    """target [n] float32 = 1e4 log(A / A_ps) - feat[:, 7] (icrs_surrogate_target)."""
+    import torch
+    n = A.numel()
+    assert A.dtype == torch.float64 and A_ps.dtype == torch.float64 and feat.dtype == torch.float32
+    if out is None:
+        out = torch.empty((n,), dtype=torch.float32, device=A.device)
+    check(lib.icrs_surrogate_target(_ptr(A), _ptr(A_ps), _ptr(feat), n, _ptr(out), _stream(torch, stream)))
+    return out
+
+
+def surrogate_batch(feat, target, idx, out_feat=None, out_target=None, stream=None):
+    """Rows idx of (feat [N, 8], target [N]) into (out_feat [n, 8], out_target [n])."""
+    import torch
+    n = idx.numel()
+    assert idx.dtype == torch.int32 and feat.is_contiguous()
+    if out_feat is None:
+        out_feat = torch.empty((n, 8), dtype=torch.float32, device=feat.device)
+    if out_target is None:
+        out_target = torch.empty((n,), dtype=torch.float32, device=feat.device)
+    check(lib.icrs_surrogate_batch(_ptr(feat), _ptr(target), _ptr(idx), n, _ptr(out_feat), _ptr(out_target),
+                                   _stream(torch, stream)))
+    return out_feat, out_target

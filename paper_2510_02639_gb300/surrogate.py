@@ -63,7 +63,7 @@ def make_dataset(n_sets: int, n_epochs: int, seed: int, grid: dict | None = None
     feat, Aps, st = icrs.surrogate_features(pd, tt, gr)
     A, _ = icrs.magnification(pd, tt, gr)
     A = A.reshape(-1)
-    target = (icrs.TARGET_SCALE * torch.log(A / Aps) - feat[:, 7].double()).to(torch.float32)
+    target = icrs.surrogate_target(A, Aps, feat)
     return Dataset(feat, Aps, st, A, target, pd, tt)
 
 
@@ -96,13 +96,14 @@ class Surrogate:
         gen.manual_seed(seed)
         total = epochs * nb
         out = []
+        fb = torch.empty((batch, 8), dtype=torch.float32, device=self.device)
+        yb = torch.empty((batch,), dtype=torch.float32, device=self.device)
         for ep in range(epochs):
-            perm = torch.randperm(n, device=self.device, generator=gen)
+            # the shuffle is an input (random draws); the gather runs in the library
+            perm = torch.randperm(n, device=self.device, generator=gen).to(torch.int32)
             acc = torch.zeros((), dtype=torch.float64, device=self.device)
             for b in range(nb):
-                idx = perm[b * batch:(b + 1) * batch]
-                fb = feat[idx].contiguous()
-                yb = y[idx].contiguous()
+                icrs.surrogate_batch(feat, y, perm[b * batch:(b + 1) * batch], fb, yb)
                 k = ep * nb + b
                 lr_k = lr_min + 0.5 * (lr - lr_min) * (1.0 + np.cos(np.pi * k / total))
                 self.step += 1
@@ -132,6 +133,24 @@ class Surrogate:
         if k:
             icrs.magnification_indexed(params_dev, t, grid, idx, k, A)
         return (A, k, idx[:k]) if return_index else (A, k)
+
+
+def preselected_magnification(params_dev, t, grid, caustic_min: float, b_max: float, n_ext: int = 0,
+                              mode: int = 1, A_max: float = 10.0, rho_min: float = 5e-4, A_small: float = 2.0,
+                              feat=None, A_ps=None, st=None, return_index=False):
+    """A [S * E] with the non-learned preselection (icrs_epoch_gate): epochs
+    near a caustic, and those within n_ext epochs of one on the same light
+    curve, run ICRS; the others get the second-order estimate (mode 1) or the
+    point-source value (mode 0).  Returns (A, number routed[, indices])."""
+    S = params_dev.numel() // icrs.PARAMS_DTYPE.itemsize
+    E = t.shape[-1]
+    if feat is None:
+        feat, A_ps, st = icrs.surrogate_features(params_dev, t, grid)
+    A, idx, nr = icrs.epoch_gate(feat, A_ps, st, S, E, n_ext, mode, b_max, caustic_min, A_max, rho_min, A_small)
+    k = int(nr.item())
+    if k:
+        icrs.magnification_indexed(params_dev, t, grid, idx, k, A)
+    return (A, k, idx[:k]) if return_index else (A, k)
 
 
 @dataclass

@@ -31,16 +31,35 @@ def test_header_symbols_exported(libmod):
         assert hasattr(libmod.lib, n), n
 
 
-def test_struct_layouts(libmod):
-    assert ctypes.sizeof(libmod.IcrsParams) == 14 * 8
-    assert ctypes.sizeof(libmod.IcrsGrid) == 8 * 4 + 3 * 8
+def test_struct_layouts(libmod, tmp_path):
+    """The binding's ctypes structs have the header's field offsets and sizes
+    (a C program compiled against include/icrs.h prints them)."""
+    import subprocess
+    inc = os.path.join(ROOT, "include")
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "icrs.h"', "int main(void) {"]
+    for st, cls in (("icrs_params", libmod.IcrsParams), ("icrs_grid", libmod.IcrsGrid)):
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["return 0;", "}"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for st, cls in (("icrs_params", libmod.IcrsParams), ("icrs_grid", libmod.IcrsGrid)):
+        assert got[(st, "size")] == ctypes.sizeof(cls), st
+        for f, _ in cls._fields_:
+            assert got[(st, f)] == getattr(cls, f).offset, (st, f)
+    assert ctypes.sizeof(libmod.IcrsParams) == libmod.PARAMS_DTYPE.itemsize == 15 * 8
     g = libmod.make_grid()
     assert (g.n_r, g.n_theta, g.n_limb, g.n_bins_r, g.n_bins_theta) == (64, 256, 500, 32, 64)
     assert abs(g.delta_c - 0.02) < 1e-15 and abs(g.margin - 0.05) < 1e-15
 
 
 def test_strerror_and_version(libmod):
-    assert libmod.lib.icrs_abi_version() == 1
+    assert libmod.lib.icrs_abi_version() == 2
     for c in range(5):
         assert libmod.lib.icrs_strerror(c)
 

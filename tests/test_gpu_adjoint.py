@@ -200,3 +200,18 @@ def test_unsupported_and_empty(G):
     t = torch.zeros((1, 0), dtype=torch.float64, device="cuda")
     grad, dA, A, st = G.magnification_vjp(pd, t, G.make_grid(), torch.zeros_like(t))
     assert torch.all(grad == 0)
+
+
+def test_dA_quadratic_limb_darkening(G, oracle_mod):
+    """Quadratic limb darkening (u2 = 0.3): dA/dp of the adjoint against the
+    oracle's FP64 forward mode on 12 epochs of the caustic-crossing curve
+    (u2 itself is not a derivative slot; it changes I0 and dI/dd, dI/drho,
+    dI/du1)."""
+    params, t = I.caustic_crossing_binary()
+    params = [dict(params[0], u2=0.3)]
+    t = t[:, ::42]
+    g = I.grid()
+    A, dA, st, grad = gpu_dA(G, params, t, g)
+    Ao, dAo, so = oracle_mod.magnification_fwd(params, t, g)
+    assert np.all(np.abs(A / Ao - 1.0) <= TAU)
+    assert_dA(dA, dAo, "quadratic LD", Ao)

@@ -40,6 +40,19 @@ def assert_parity(A, Ao, tol=TOL, what=""):
     assert len(bad) == 0, f"{what}: {len(bad)} of {rel.size} above {tol}; worst {rel.max():.3e} at {np.unravel_index(rel.argmax(), rel.shape)}"
 
 
+# Status bits that the GPU and the oracle define the same way: illegal image
+# count, merged sectors (cap), grid edge, non-finite result.  (Non-convergence
+# depends on each side's own iteration; table overflow exists on the GPU only.)
+SHARED_BITS = 2 | 4 | 8 | 16
+
+
+def assert_status(st, so, what=""):
+    a = np.asarray(st).astype(np.int64) & SHARED_BITS
+    b = np.asarray(so).astype(np.int64) & SHARED_BITS
+    bad = np.argwhere(a != b)
+    assert len(bad) == 0, f"{what}: status bits differ at {bad[:5].tolist()}: gpu {a[tuple(bad[0])]} oracle {b[tuple(bad[0])]}"
+
+
 def test_point_source_binary(G, oracle_mod):
     import torch
     rng = np.random.default_rng(21)
@@ -77,6 +90,7 @@ def test_caustic_crossing_curve(G, oracle_mod):
     A, st = run_gpu(G, params, t, g)
     Ao, so = oracle_mod.magnification(params, t, g)
     assert_parity(A, Ao, what="caustic crossing")
+    assert_status(st, so, what="caustic crossing")
     assert not np.any(st & 16)
 
 
@@ -89,6 +103,7 @@ def test_binary_batch_small(G, oracle_mod):
     A, st = run_gpu(G, params, t, g)
     Ao, so = oracle_mod.magnification(params, t, g)
     assert_parity(A, Ao, what="binary batch")
+    assert_status(st, so, what="binary batch")
 
 
 def test_triple_curve(G, oracle_mod):
@@ -99,6 +114,7 @@ def test_triple_curve(G, oracle_mod):
     A, st = run_gpu(G, params, t, g)
     Ao, so = oracle_mod.magnification(params, t, g)
     assert_parity(A, Ao, what="triple")
+    assert_status(st, so, what="triple")
 
 
 def test_uniform_and_grid_variants(G, oracle_mod):
@@ -108,6 +124,7 @@ def test_uniform_and_grid_variants(G, oracle_mod):
         A, st = run_gpu(G, params, t, g)
         Ao, so = oracle_mod.magnification(params, t, g)
         assert_parity(A, Ao, what=str(g))
+        assert_status(st, so, what=str(g))
 
 
 def test_ring_and_origin_cases(G, oracle_mod):
@@ -140,22 +157,55 @@ def test_full_batch_sampled(G, oracle_mod):
         assert abs(A[s, e] / Ao[0, 0] - 1.0) <= TOL, (s, e, A[s, e], Ao[0, 0])
 
 
-def test_headline_grid_full_batch_sampled(G, oracle_mod):
+@pytest.fixture(scope="module")
+def headline(G):
     """The benchmark's headline launch: the 64 x 10,000 batch in one call at
-    n_r = 1024, n_theta = 2048 (the 768-thread binary kernel, 508-ray row
-    segments, warm starts along each light curve).  The oracle recomputes 24
-    sampled epochs on the same grid: the highest-magnification epoch of 8
-    sets and 16 random ones."""
+    n_r = 1024, n_theta = 2048 (warm starts along each light curve)."""
     params, t = I.binary_batch()
     g = I.grid(n_r=1024, n_theta=2048)
     A, st = run_gpu(G, params, t, g)
+    return params, t, g, A, st
+
+
+def test_headline_grid_full_batch_sampled(headline, oracle_mod):
+    """The oracle recomputes 24 sampled epochs of the headline launch on the
+    same grid: the highest-magnification epoch of 8 sets and 16 random ones."""
+    params, t, g, A, st = headline
     assert np.all(np.isfinite(A))
     rng = np.random.default_rng(7)
     picks = [(s, int(np.argmax(A[s]))) for s in range(0, len(params), 8)]
     picks += [(int(rng.integers(len(params))), int(rng.integers(t.shape[1]))) for _ in range(16)]
     for s, e in picks:
-        Ao, _ = oracle_mod.magnification([params[s]], [t[s, e]], g)
+        Ao, so = oracle_mod.magnification([params[s]], [t[s, e]], g)
         assert abs(A[s, e] / Ao[0, 0] - 1.0) <= TOL, (s, e, A[s, e], Ao[0, 0])
+        assert (int(st[s, e]) & SHARED_BITS) == (int(so[0, 0]) & SHARED_BITS), (s, e, st[s, e], so[0, 0])
+
+
+def test_headline_merged_sector_epochs(G, headline, oracle_mod):
+    """Every epoch of the headline launch whose sectors reached the cap and
+    were merged (ICRS_ST_SECTCAP), the epochs where the sector rule is most
+    sensitive to the image-limb points: each against the oracle (cold roots)
+    at 1e-5 with the same status bits, and the indexed launch of just those
+    epochs (roots warm-started from an unrelated epoch) equal to the full
+    launch to 1e-7."""
+    import torch
+    params, t, g, A, st = headline
+    idx = [(int(s), int(e)) for s, e in np.argwhere(st & 4)]
+    assert idx, "the headline workload has merged-sector epochs"
+    for s, e in idx:
+        Ao, so = oracle_mod.magnification([params[s]], [t[s, e]], g)
+        assert abs(A[s, e] / Ao[0, 0] - 1.0) <= TOL, (s, e, A[s, e], Ao[0, 0])
+        assert (int(st[s, e]) & SHARED_BITS) == (int(so[0, 0]) & SHARED_BITS), (s, e, st[s, e], so[0, 0])
+    S, E = t.shape
+    pd = G.params_to_device(params)
+    tt = torch.tensor(t, device="cuda")
+    items = torch.tensor([s * E + e for s, e in idx], dtype=torch.int32, device="cuda")
+    Ai = torch.full((S, E), float("nan"), dtype=torch.float64, device="cuda")
+    sti = torch.zeros((S, E), dtype=torch.int32, device="cuda")
+    G.magnification_indexed(pd, tt, G.grid_from_dict(g, 2), items, len(idx), Ai, sti)
+    Ai = Ai.cpu().numpy()
+    for s, e in idx:
+        assert abs(Ai[s, e] / A[s, e] - 1.0) <= 1e-7, (s, e, Ai[s, e], A[s, e])
 
 
 def test_wide_theta_grid(G, oracle_mod):
@@ -178,3 +228,23 @@ def test_empty_and_invalid(G):
     assert A.shape == (1, 0)
     with pytest.raises(G.IcrsError):
         G.magnification(pd, torch.zeros((1, 3), dtype=torch.float64, device="cuda"), G.make_grid(n_theta=4))
+
+
+def test_quadratic_limb_darkening_and_split_rule(G, oracle_mod):
+    """Quadratic limb darkening (u2 = 0.25) on the caustic-crossing curve,
+    with the literal per-point rule and the split-profile rule, and the
+    linear law with the split rule: each against the oracle at 1e-5 with the
+    same status bits.  The derivative entry points refuse the split rule."""
+    import torch
+    base, t = I.caustic_crossing_binary(n_epochs=60)
+    for u2, split in ((0.25, 0), (0.25, 1), (0.0, 1)):
+        params = [dict(base[0], u2=u2)]
+        g = I.grid(ld_split=split)
+        A, st = run_gpu(G, params, t, g)
+        Ao, so = oracle_mod.magnification(params, t, g)
+        assert_parity(A, Ao, what=f"u2={u2} split={split}")
+        assert_status(st, so, what=f"u2={u2} split={split}")
+    pd = G.params_to_device(base)
+    tt = torch.tensor(t, device="cuda")
+    with pytest.raises(G.IcrsError):
+        G.magnification_vjp(pd, tt, G.grid_from_dict(I.grid(ld_split=1), 2), torch.ones_like(tt))

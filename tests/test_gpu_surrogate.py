@@ -2,14 +2,21 @@
 (oracle/mlp.py): tcgen05 inference, the training step's gradient and Adam
 update, the feature kernel, the gate and the indexed ICRS launch.
 
-Tolerance of the network outputs and gradients.  The oracle mirrors every BF16
-rounding point, and its contractions are exact in FP64.  The GPU accumulates
-in FP32.  So a value that lies within ~1e-7 of a BF16 rounding boundary can
-round the other way.  Such a 1-ulp flip moves that activation by 2^-8 of its
-value and propagates.  The bound for each output is therefore 2^-8 of the
-largest activation-weighted term; the checks use 1e-2 of max |Y| for any
-element and 1e-4 of max |Y| for the median element.  For the gradient:
-relative L2 error <= 1e-2 per layer.
+Reference network: BF16-rounded weights and inputs, every other operation
+exact in FP64 (oracle/mlp.py reference_forward).  The kernels in addition
+round each hidden activation to BF16 (their tensor-core operands), round the
+upstream gradient of each layer to BF16 in the backward pass, and accumulate
+in FP32.  Element-wise tolerances:
+  - inference output Y[n, j]: 1.5 x the first-order bound of
+    inference_bound, sum_l |dY_j/dX_l| . 2^-8 |X_l| plus the FP32
+    accumulation terms (a rigorous bound to first order; 1.5 covers the
+    second-order remainder);
+  - gradient entry g: 4 x 2^-8 x sum_n |term_n| over the batch's terms of that
+    entry (gradient_term_scale): each term dZ_l[n, j] X_l[n, i] carries the
+    rounding of its two factors (2 x 2^-8) plus the propagated roundings of
+    earlier layers, which are smaller; 4 leaves a factor of two.
+The network with every kernel rounding mirrored (forward(bf16=True)) is
+printed beside them as a diagnostic only.
 """
 import numpy as np
 import pytest
@@ -61,12 +68,13 @@ def test_infer_matches_oracle(G):
     pack = G.mlp_pack(tt)
     out = G.mlp_infer(pack, tt, torch.tensor(f, device="cuda"), err=err).cpu().numpy()
     assert int(err.item()) == 0
-    Yo, _ = M.forward(th, f[:, :7].astype(np.float64), bf16=True)
-    d = np.abs(out - Yo)
-    sc = np.abs(Yo).max()
-    print("infer max", d.max() / sc, "median", np.median(d) / sc)
     assert np.all(np.isfinite(out))
-    assert d.max() <= 1e-2 * sc and np.median(d) <= 1e-4 * sc
+    Yr, bound = M.inference_bound(th, f[:, :7].astype(np.float64))
+    ratio = np.abs(out - Yr) / (1.5 * bound + 1e-30)
+    Ym, _ = M.forward(th, f[:, :7].astype(np.float64), bf16=True)
+    print("infer |gpu - ref| / (1.5 bound): max", ratio.max(), "median", np.median(ratio),
+          "| diagnostic, mirrored network: max |gpu - mirror| / bound", (np.abs(out - Ym) / bound).max())
+    assert np.all(ratio <= 1.0), (np.argwhere(ratio > 1.0)[:5], ratio.max())
 
 
 def test_gradient_and_loss_match_oracle(G):
@@ -84,17 +92,23 @@ def test_gradient_and_loss_match_oracle(G):
     G.mlp_train_step(tt, None, None, pack, 1, 0.0, torch.tensor(f, device="cuda"), torch.tensor(y, device="cuda"),
                      grad=grad, loss=loss, err=err)
     assert int(err.item()) == 0
-    Yo, cache = M.forward(th, f[:, :7].astype(np.float64), bf16=True)
-    Lo, dY = M.nll(Yo, y.astype(np.float64))
-    go = M.backward(cache, dY)
+    X = f[:, :7].astype(np.float64)
+    gr, scale, Lr = M.gradient_term_scale(th, X, y.astype(np.float64))
     g = grad.cpu().numpy().astype(np.float64)
-    assert abs(float(loss.item()) - Lo) <= 1e-3 * abs(Lo) + 1e-6
+    # loss: the first-order effect of the outputs' bound
+    Yr, bY = M.inference_bound(th, X)
+    _, dY = M.nll(Yr, y.astype(np.float64))
+    assert abs(float(loss.item()) - Lr) <= 1.5 * float(np.sum(np.abs(dY) * bY)) + 1e-6 * abs(Lr)
+    tol = 4.0 * M.U_BF16 * scale + 1e-12
+    Ym, cache = M.forward(th, X, bf16=True)
+    gm = M.backward(cache, M.nll(Ym, y.astype(np.float64))[1])
     offs = np.cumsum([0] + [int(np.prod(s)) for _, s in M.SHAPES])
     for i, (name, _) in enumerate(M.SHAPES):
-        a, b = g[offs[i]:offs[i + 1]], go[offs[i]:offs[i + 1]]
-        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-        print(name, "grad rel L2", rel)
-        assert rel <= 1e-2, (name, rel)
+        sl = slice(offs[i], offs[i + 1])
+        ratio = np.abs(g[sl] - gr[sl]) / tol[sl]
+        print(name, "grad |gpu - ref| / tol: max", ratio.max(), "| diagnostic, |gpu - mirror| / tol:",
+              (np.abs(g[sl] - gm[sl]) / tol[sl]).max())
+        assert np.all(ratio <= 1.0), (name, np.argwhere(ratio > 1.0)[:5], ratio.max())
 
 
 def test_adam_step_matches_oracle(G):
@@ -239,3 +253,42 @@ def test_surrogate_gain_over_plain_icrs(G):
     assert k < n
     assert n - k > int(ps_ok.sum())
     assert t_gate < t_plain
+
+
+def test_epoch_preselection_gate(G):
+    """Non-learned preselection (icrs_epoch_gate): the near-caustic flags, the
+    n_ext extension along each light curve and the ordered routed list equal
+    a numpy evaluation of the same rule on the kernel's own features; the
+    accepted epochs carry the second-order estimate (mode 1) or A_ps (mode
+    0) exactly; the routed epochs through the indexed launch equal the full
+    launch."""
+    import torch
+    params, t = I.binary_batch(n_sets=3, n_epochs=700, seed=43)
+    g = G.grid_from_dict(I.grid(), 2)
+    pd = G.params_to_device(params)
+    tt = torch.tensor(t, device="cuda")
+    S, E = t.shape
+    feat, Aps, st = G.surrogate_features(pd, tt, g)
+    f_ = feat.cpu().numpy(); a_ = Aps.cpu().numpy(); s_ = st.cpu().numpy()
+    Afull, _ = G.magnification(pd, tt, g)
+    Af = Afull.cpu().numpy().ravel()
+    for n_ext, mode, c_min, b_max in ((0, 1, -1.0, 3.0), (4, 1, -1.5, 10.0), (2, 0, -0.5, 1.0)):
+        A, idx, nr = G.epoch_gate(feat, Aps, st, S, E, n_ext, mode, b_max, c_min, A_max=10.0, rho_min=5e-4,
+                                  A_small=2.0)
+        k = int(nr.item())
+        near = ~((s_ == 0) & (f_[:, 6] >= c_min) & (np.abs(f_[:, 7]) <= b_max)
+                 & (a_ <= np.where(f_[:, 4] >= np.float32(np.log10(np.float32(5e-4))) + np.float32(3.0), 10.0, 2.0)))
+        nb = near.reshape(S, E)
+        routed = np.zeros_like(nb)
+        for s in range(S):
+            for e in np.flatnonzero(nb[s]):
+                routed[s, max(0, e - n_ext): e + n_ext + 1] = True
+        routed = routed.ravel()
+        np.testing.assert_array_equal(idx.cpu().numpy()[:k], np.flatnonzero(routed))
+        Ah = A.cpu().numpy()
+        ok = ~routed
+        est = a_[ok] * (np.exp(f_[ok, 7].astype(np.float64) * 1e-4) if mode == 1 else 1.0)
+        np.testing.assert_allclose(Ah[ok], est, rtol=1e-12)
+        G.magnification_indexed(pd, tt, g, idx, k, A)
+        np.testing.assert_allclose(A.cpu().numpy()[routed], Af[routed], rtol=1e-7)
+        assert 0 < k < S * E
