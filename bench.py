@@ -8,10 +8,11 @@ Headline workload: the 64-set binary batch with 10,000 epochs per set.
   - epochs uniform in [t0 - 2 tE, t0 + 2 tE];
   - 500 limb points, and the accuracy-qualified polar grid of 1024 x 2048
     rays per sector.
-The qualification is measured in the same run. The GPU magnifications of 48
-sampled epochs are compared with the oracle's converged 2048 x 4096 values
-(tests/golden/batch_converged.json), and the line reports the maximum
-relative error. The fixed 64 x 256 grid is measured as a secondary line with
+The qualification is measured in the same run. The GPU magnifications of
+the 512-epoch qualification sample are compared with the oracle's 4096 x
+8192 values (tests/golden/batch_qualification.json), whose own error is
+bounded by their last Richardson difference; the line reports the error
+distribution. The fixed 64 x 256 grid is measured as a secondary line with
 its own measured error, which is above 1e-4.
 
 One step is one call of icrs_magnification over the whole batch, a single
@@ -53,7 +54,7 @@ FLOPS_PER_RAY = {2: 30.0, 3: 40.0}   # algorithmic FP32 flops per ray (lens map 
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 HEADLINE_GRID = dict(n_r=1024, n_theta=2048)
 FIXED_GRID = dict(n_r=64, n_theta=256)
-GOLDEN = os.path.join(ROOT, "tests", "golden", "batch_converged.json")
+GOLDEN = os.path.join(ROOT, "tests", "golden", "batch_qualification.json")
 
 
 def peaks():
@@ -157,8 +158,9 @@ def grid_desc(g):
 
 
 def run_reference(args, rank, world):
-    """FP64 oracle on the host cores at the headline grid: each step one
-    bounded sample of (set, epoch) pairs of the workload (single thread)."""
+    """FP64 oracle on all host cores (its OpenMP-over-epochs build) at the
+    headline grid: each step one bounded sample of (set, epoch) pairs of the
+    workload."""
     if rank != 0:
         return
     import oracle
@@ -168,11 +170,13 @@ def run_reference(args, rank, world):
     rng = np.random.default_rng(7)
     n = args.ref_sample
     picks = [(int(rng.integers(len(params))), int(rng.integers(t.shape[1]))) for _ in range(n)]
-    oracle.build()
+    ps = [params[s] for s, _ in picks]
+    tp = np.array([[t[s, e]] for s, e in picks])
+    oracle.build_omp()
+    cores = os.cpu_count() or 1
 
     def step():
-        for s, e in picks:
-            oracle.magnification([params[s]], [t[s, e]], g)
+        oracle.magnification_all_cores(ps, tp, g)
 
     for _ in range(args.warmup):
         step()
@@ -185,14 +189,18 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": dict(desc, grid=grid_desc(HEADLINE_GRID), n_limb=500),
-            "cpu_baseline": {"value": val, "unit": "magnifications/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{n} random (set, epoch) pairs of the workload per step"},
+            "cpu_baseline": {"value": val, "unit": "magnifications/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} random (set, epoch) pairs of the workload per step, OpenMP over "
+                                       f"epochs on {cores} host cores"},
             "e2e": {"value": val, "unit": "magnifications/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(params, t, g, seconds=12.0):
+def cpu_baseline(params, t, g, seconds=10.0):
+    """The oracle as it stands on the host: one thread (random single epochs
+    for ~seconds), and its OpenMP build on all cores (a fixed sample sized
+    for about the same time)."""
     import oracle
     oracle.build()
     rng = np.random.default_rng(11)
@@ -203,26 +211,76 @@ def cpu_baseline(params, t, g, seconds=12.0):
         oracle.magnification([params[s]], [t[s, e]], g)
         n += 1
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "magnifications/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} random (set, epoch) pairs of the workload at {grid_desc(g)}, FP64 single thread, "
-                      f"{dt:.1f} s"}
+    one = n / dt
+    cores = os.cpu_count() or 1
+    m = max(cores, int(one * seconds * cores * 0.8))
+    picks = [(int(rng.integers(len(params))), int(rng.integers(t.shape[1]))) for _ in range(m)]
+    oracle.build_omp()
+    t1 = time.perf_counter()
+    oracle.magnification_all_cores([params[s] for s, _ in picks], np.array([[t[s, e]] for s, e in picks]), g)
+    dt_all = time.perf_counter() - t1
+    return {"value": m / dt_all, "unit": "magnifications/s", "cores": cores, "kind": "oracle",
+            "sample": f"{m} random (set, epoch) pairs of the workload at {grid_desc(g)}, FP64, OpenMP over epochs "
+                      f"on {cores} host cores, {dt_all:.1f} s",
+            "single_core": {"value": one, "cores": 1,
+                            "sample": f"{n} random (set, epoch) pairs, one thread, {dt:.1f} s"}}
 
 
 def accuracy(icrs, I, g, dev):
-    """Maximum relative error of the GPU magnification against the oracle's
-    converged values of the sampled batch epochs."""
+    """Relative error of the GPU magnification at grid g on the 512-epoch
+    qualification sample of the batch (tests/golden/batch_qualification.json:
+    every set's peak epoch, random epochs, small sources at moderate
+    magnification, sources inside a caustic) against the oracle's finest
+    grid (4096 x 8192), whose own error is bounded by its last Richardson
+    difference (4096 x 8192 against 2048 x 4096)."""
     import torch
     gold = json.load(open(GOLDEN))
     params, t = I.binary_batch()
-    ps = [params[r["set"]] for r in gold["epochs"]]
-    tp = torch.tensor([[t[r["set"], r["epoch"]]] for r in gold["epochs"]], dtype=torch.float64, device=dev)
-    ref = np.array([r["A"] for r in gold["epochs"]])
+    rows = gold["epochs"]
+    ps = [params[r["set"]] for r in rows]
+    tp = torch.tensor([[t[r["set"], r["epoch"]]] for r in rows], dtype=torch.float64, device=dev)
+    ref = np.array([r["A"][-1] for r in rows])
+    ref_err = np.abs(np.array([r["A"][-1] / r["A"][-2] - 1.0 for r in rows]))
     A, _ = icrs.magnification(icrs.params_to_device(ps, dev), tp, icrs.grid_from_dict(g, 2))
     e = np.abs(A.cpu().numpy().ravel() / ref - 1.0)
+    cls = np.array([r["class"] for r in rows])
+    fine = gold["grids"][-1]
     return {"max_rel_err": float(e.max()), "p99_rel_err": float(np.quantile(e, 0.99)),
-            "median_rel_err": float(np.median(e)), "n": int(len(e)),
-            "reference": f"FP64 oracle at {gold['grid']['n_r']}x{gold['grid']['n_theta']}, "
-                         f"tests/golden/batch_converged.json"}
+            "median_rel_err": float(np.median(e)), "n": int(len(e)), "n_above_1e-4": int((e > 1e-4).sum()),
+            "n_certified_1e-4": int(((e + ref_err) <= 1e-4).sum()),
+            "max_rel_err_by_class": {c: float(e[cls == c].max()) for c in sorted(set(cls))},
+            "reference_max_richardson_bound": float(ref_err.max()),
+            "reference": f"FP64 oracle at {fine['n_r']}x{fine['n_theta']} (error bound: its difference from "
+                         f"the previous doubling), tests/golden/batch_qualification.json"}
+
+
+def accuracy_triple(icrs, I, g, dev):
+    """Relative error of the GPU on the 32 triple-lens epochs of
+    tests/golden/triple_qualification.json against the oracle at the finest
+    grid (4096 x 8192) and, for parity, on the same grid."""
+    import torch
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "triple_qualification.json")))
+    params, t = I.triple_curve()
+    rows = gold["epochs"]
+    tp = torch.tensor([[t[0, r["epoch"]] for r in rows]], dtype=torch.float64, device=dev)
+    A, _ = icrs.magnification(icrs.params_to_device(params, dev), tp, icrs.grid_from_dict(g, 3))
+    A = A.cpu().numpy().ravel()
+    ref = np.array([r["A"][-1] for r in rows])
+    same = [r["A"][[(x["n_r"], x["n_theta"]) for x in gold["grids"]].index((g["n_r"], g["n_theta"]))]
+            for r in rows] if any((x["n_r"], x["n_theta"]) == (g["n_r"], g["n_theta"]) for x in gold["grids"]) else None
+    e = np.abs(A / ref - 1.0)
+    out = {"max_rel_err": float(e.max()), "median_rel_err": float(np.median(e)), "n": int(len(e)),
+           "reference_max_richardson_bound": float(np.max(np.abs([r["A"][-1] / r["A"][-2] - 1.0 for r in rows]))),
+           "reference": "FP64 oracle at 4096x8192, tests/golden/triple_qualification.json"}
+    if same is not None:
+        out["max_rel_err_vs_oracle_same_grid"] = float(np.max(np.abs(A / np.array(same) - 1.0)))
+    return out
+
+
+def secondary_steps(args):
+    """Timed and warm-up steps of the secondary lines (at most 3 each, so
+    that a long headline run does not multiply their cost)."""
+    return max(1, min(args.steps, 3)), max(1, min(args.warmup, 3))
 
 
 def timed_steps(fn, steps, warmup, flush, stream):
@@ -258,14 +316,15 @@ def chi2_bench(icrs, I, args, dev, stream, flush, n_sets, grid=None):
     def step():
         out["r"] = icrs.chi2_grad(pd, tt, g, y, sig, stream=stream)
 
-    ms = timed_steps(step, args.steps, args.warmup, flush, stream)
+    steps, warm = secondary_steps(args)
+    ms = timed_steps(step, steps, warm, flush, stream)
     sec = float(np.sum(ms)) / 1e3
     grad = out["r"][1]
-    return {"value": len(params) * args.steps / sec, "unit": "chi^2 gradients/s",
-            "epochs_per_s": len(params) * t.shape[1] * args.steps / sec,
-            "ms_per_step": sec / args.steps * 1e3, "steps": args.steps, "warmup": args.warmup,
+    return {"value": len(params) * steps / sec, "unit": "chi^2 gradients/s",
+            "epochs_per_s": len(params) * t.shape[1] * steps / sec,
+            "ms_per_step": sec / steps * 1e3, "steps": steps, "warmup": warm,
             "workload": f"adjoint_batch_{len(params)}x{t.shape[1]}", "grid": grid_desc(grid), "params": 8,
-            "dtype": "f32", "finite": bool(torch.isfinite(grad).all().item()), "gpu_launches": args.steps}
+            "dtype": "f32", "finite": bool(torch.isfinite(grad).all().item()), "gpu_launches": steps}
 
 
 def chi2_accuracy(icrs, I, dev, grid, n_epochs=12):
@@ -318,14 +377,16 @@ def nll_bench(icrs, I, args, dev, stream, flush, n_sets, grid):
     def step():
         out["r"] = icrs.marginal_nll_grad(pd, tt, g, F, sig, prior, workspace=ws, stream=stream)
 
-    ms = timed_steps(step, args.steps, args.warmup, flush, stream)
+    steps, warm = secondary_steps(args)
+    ms = timed_steps(step, steps, warm, flush, stream)
     sec = float(np.sum(ms)) / 1e3
     nll, grad, fl = out["r"][0], out["r"][1], out["r"][2]
-    return {"value": len(params) * args.steps / sec, "unit": "marginal NLL gradients/s",
-            "epochs_per_s": len(params) * t.shape[1] * args.steps / sec,
-            "ms_per_step": sec / args.steps * 1e3, "workload": f"adjoint_batch_{len(params)}x{t.shape[1]}",
+    return {"value": len(params) * steps / sec, "unit": "marginal NLL gradients/s",
+            "epochs_per_s": len(params) * t.shape[1] * steps / sec,
+            "ms_per_step": sec / steps * 1e3, "steps": steps, "warmup": warm,
+            "workload": f"adjoint_batch_{len(params)}x{t.shape[1]}",
             "grid": grid_desc(grid), "params": 8, "finite": bool(torch.isfinite(grad).all().item()),
-            "flux_posterior_mean": [float(x) for x in fl.mean(0).tolist()], "gpu_launches": 2 * args.steps}
+            "flux_posterior_mean": [float(x) for x in fl.mean(0).tolist()], "gpu_launches": 2 * steps}
 
 
 def surrogate_bench(args, dev):
@@ -383,6 +444,23 @@ def surrogate_bench(args, dev):
     Aest = Aps * torch.exp(feat[:, 7].double() / icrs.TARGET_SCALE)
     est_err = torch.where(est_ok, (Aest / Ap - 1.0).abs(), torch.zeros_like(err))
     t_plain, t_gate = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    # the non-learned preselection through the library (icrs_epoch_gate +
+    # indexed ICRS), calibrated like the estimate rule, without and with an
+    # n_ext = 2 extension along each light curve
+    presel = {}
+    for n_ext in (0, 2):
+        ee = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ee[0].record()
+        A_pre, k_pre = SG.preselected_magnification(pd, tt, g, c_est, b_est, n_ext=n_ext, mode=1,
+                                                    A_max=gate.A_max, rho_min=gate.rho_min, A_small=gate.A_small)
+        ee[1].record()
+        torch.cuda.synchronize()
+        t_pre = ee[0].elapsed_time(ee[1])
+        err_pre = (A_pre / Ap - 1.0).abs()
+        presel[f"n_ext_{n_ext}"] = {"speedup": t_plain / t_pre, "routed_frac": k_pre / n, "ms": t_pre,
+                                    "max_rel_err": float(err_pre.max()),
+                                    "n_above_1e-4": int((err_pre > 1e-4).sum())}
     return {"speedup": t_plain / t_gate, "queries": n, "routed_frac": k / n,
             "max_rel_err_vs_plain": float(err.max()),
             "vs_plain": {"accepted": err_stats(~routed), "routed_plain_unflagged": err_stats(routed & ~flagged),
@@ -402,6 +480,7 @@ def surrogate_bench(args, dev):
             "second_order_estimate_only": {"accepted_frac": float(est_ok.float().mean()), "caustic_min": c_est,
                                            "b_max": b_est,
                                            "max_rel_err": float(est_err.max())},
+            "preselection_gate": presel,
             "dtype": "bf16 weights / fp32 accumulate"}
 
 
@@ -412,13 +491,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="icrs", choices=["icrs", "reference"])
     ap.add_argument("--workload", default="batch", choices=["batch", "caustic", "triple"])
-    ap.add_argument("--ref-sample", type=int, default=6, help="oracle epochs per reference step")
+    ap.add_argument("--ref-sample", type=int, default=64, help="oracle epochs per reference step (all host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chi2-sets", type=int, default=256, help="sets of the adjoint batch per chi^2 step (0: skip)")
     ap.add_argument("--chi2-sets-qualified", type=int, default=8,
                     help="sets of the adjoint batch per chi^2 step at the headline grid (0: skip)")
-    ap.add_argument("--sur-train-sets", type=int, default=200, help="surrogate training sets x 2000 epochs (0: skip)")
-    ap.add_argument("--sur-query-sets", type=int, default=250, help="surrogate scoring sets x 2000 epochs")
+    ap.add_argument("--sur-train-sets", type=int, default=1000,
+                    help="surrogate training sets x 2000 epochs (0: skip); 1000 = the configuration's 2M samples")
+    ap.add_argument("--sur-query-sets", type=int, default=5000,
+                    help="surrogate scoring sets x 2000 epochs; 5000 = the configuration's 10M queries")
     ap.add_argument("--sur-epochs", type=int, default=30)
     ap.add_argument("--clocks-csv", default="", help="where the nvidia-smi samples of the timed steps go "
                                                      "({rank} is replaced); default /tmp/clocks_rank{rank}.csv")
@@ -504,7 +585,7 @@ def main():
     d_params = torch.empty_like(pd)
     d_t = torch.empty_like(tt)
     torch.cuda.synchronize()
-    n_e2e = max(1, args.steps)
+    n_e2e = secondary_steps(args)[0]
     w0 = time.perf_counter()
     for _ in range(n_e2e):
         d_params.copy_(h_params, non_blocking=True)
@@ -518,15 +599,17 @@ def main():
            "h2d_bytes_per_step": int(h_params.numel() + h_t.numel() * 8),
            "d2h_bytes_per_step": int(h_A.numel() * 8 + h_st.numel() * 4)}
 
-    acc = accuracy(icrs, I, g, dev) if args.workload == "batch" else None
+    acc = accuracy(icrs, I, g, dev) if args.workload == "batch" else (
+        accuracy_triple(icrs, I, g, dev) if args.workload == "triple" else None)
 
     # the fixed 64 x 256 grid (secondary)
     gf = I.grid(**FIXED_GRID)
     gridf = icrs.grid_from_dict(gf, n_lens)
-    msf = timed_steps(lambda: icrs.magnification(pd, tt, gridf, out=A, status=st, stream=stream), args.steps,
-                      args.warmup, flush, stream)
+    fs, fw = secondary_steps(args)
+    msf = timed_steps(lambda: icrs.magnification(pd, tt, gridf, out=A, status=st, stream=stream), fs, fw, flush,
+                      stream)
     fixed = {"grid": grid_desc(gf),
-             "value": job_rate(S * E, world, args.steps, reduce_max(float(np.sum(msf)) / 1e3, world, dev)),
+             "value": job_rate(S * E, world, fs, reduce_max(float(np.sum(msf)) / 1e3, world, dev)),
              "unit": "magnifications/s", "ms_per_step": float(np.mean(msf)),
              "accuracy": accuracy(icrs, I, gf, dev) if args.workload == "batch" else None}
 

@@ -92,7 +92,7 @@ typedef struct {
  *   n_r, n_theta   polar grid per sector (Sec. 3.3): 1..4096, 8..8192
  *   n_limb         source-limb points (Sec. 3.2): 16..1024
  *   n_bins_r       radial bins per angular interval: 2..32
- *   n_bins_theta   angular bins over [-pi, pi): 2..64
+ *   n_bins_theta   angular bins over [-pi, pi): 2..128
  *   max_iter       cap on root iterations
  *   uniform        1: uniform source (Appendix A.1 rule), 0: limb darkening
  *                  (u1, u2 of the parameter set)
@@ -108,6 +108,15 @@ typedef struct {
  *                  the edge like a square root, takes f(delta).  Forward
  *                  entry points only (the derivative ones return
  *                  ICRS_EUNSUPPORTED).
+ *   grad_rule      derivative entry points: 0 = the exact almost-everywhere
+ *                  derivative of the discrete method; 1 = the paper's
+ *                  gradient rules (Sec. 3.5): the inclusion indicator chi =
+ *                  Theta(x), x = (rho - d)/rho, gets the derivative of a
+ *                  sigmoid of steepness s_fac, S s (1 - s) with s = 1/(1 +
+ *                  e^{-S x}), on every ray with the interior weight, and the
+ *                  limb-darkening correction f(delta) the fixed derivative
+ *                  2/3 of its second-order branch.  Values are unchanged.
+ *   s_fac          steepness S of that sigmoid (> 0 when grad_rule = 1)
  */
 typedef struct {
   int32_t n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter, uniform;
@@ -115,11 +124,14 @@ typedef struct {
                       from the first set on the device, which synchronises `stream` */
   double delta_c, margin, img_tol;
   int32_t ld_split;
-  int32_t reserved;
+  int32_t grad_rule;
+  double s_fac;
 } icrs_grid;
 
-/* Fills `g` with the library defaults (64 x 256 grid, 500 limb points, 32 x 64
- * bins, delta_c = 0.02, margin = 0.05, img_tol = 1e-3, linear LD, n_lens = 2). */
+/* Fills `g` with the library defaults (64 x 256 grid, 500 limb points, 32 x 128
+ * bins, delta_c = 0.02, margin = 0.05, img_tol = 1e-3, limb darkening, the
+ * literal boundary rule, the exact derivative (grad_rule = 0, s_fac = 100),
+ * n_lens = 2). */
 void icrs_grid_default(icrs_grid* g);
 
 /*

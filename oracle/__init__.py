@@ -25,7 +25,7 @@ _lib = None
 PARAM_FIELDS = ("t0", "tE", "u0", "alpha", "rho", "u1", "n_lens",
                 "s", "q", "q2", "q3", "s2", "s3", "psi", "u2")
 GRID_FIELDS = ("n_r", "n_theta", "n_limb", "n_bins_r", "n_bins_theta",
-               "max_iter", "uniform", "delta_c", "margin", "img_tol", "ld_split")
+               "max_iter", "uniform", "delta_c", "margin", "img_tol", "ld_split", "grad_rule", "s_fac")
 
 
 def build(force: bool = False) -> str:
@@ -40,6 +40,50 @@ def build(force: bool = False) -> str:
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
+
+
+_OMP_PATH = os.path.join(_HERE, "libicrs_oracle_omp.so")
+_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source compiled with OpenMP: orc_magnification runs its
+    epochs on all host cores (the CPU baseline's all-core rate)."""
+    with _lock:
+        if (not force and os.path.exists(_OMP_PATH)
+                and os.path.getmtime(_OMP_PATH) >= os.path.getmtime(_SRC)):
+            return _OMP_PATH
+        tmp = _OMP_PATH + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+               "-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OMP_PATH)
+        return _OMP_PATH
+
+
+def magnification_all_cores(params, t, grid: dict):
+    """magnification() through the OpenMP build (threads: OMP_NUM_THREADS,
+    else all cores).  Returns (A, status)."""
+    global _omp
+    if _omp is None:
+        build_omp()
+        L = ctypes.CDLL(_OMP_PATH)
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.orc_magnification.argtypes = [dp, ctypes.c_int, dp, ctypes.c_int, dp, dp,
+                                        ctypes.POINTER(ctypes.c_uint32)]
+        _omp = L
+    if isinstance(params, dict):
+        params = [params]
+    prm = np.stack([param_vector(p) for p in params])
+    S = prm.shape[0]
+    t = np.asarray(t, dtype=np.float64).reshape(S, -1)
+    E = t.shape[1]
+    prm, pp = _d(prm); t, tp = _d(t)
+    g, gp = _d(grid_vector(grid))
+    A = np.zeros((S, E)); st = np.zeros((S, E), dtype=np.uint32)
+    _omp.orc_magnification(pp, S, tp, E, gp, A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    return A, st
 
 
 def lib():

@@ -35,6 +35,7 @@
 #include <cstring>
 #include <cstdlib>
 #include <vector>
+#include <type_traits>
 #include <algorithm>
 
 namespace {
@@ -99,13 +100,13 @@ typedef Cx<double> C;
 // Inputs (flat arrays so the Python side needs no shared struct definition).
 // params[15] = t0, tE, u0, alpha, rho, u1, n_lens, s, q, q2, q3, s2, s3, psi,
 //              u2
-// grid[11]   = n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter,
-//              uniform, delta_c, margin, img_tol, ld_split
+// grid[13]   = n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter,
+//              uniform, delta_c, margin, img_tol, ld_split, grad_rule, s_fac
 // ----------------------------------------------------------------------------
 const int NPRM = 15;  // slots of one parameter set
 struct Grid {
-  int n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter, uniform, ld_split;
-  double delta_c, margin, img_tol;
+  int n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter, uniform, ld_split, grad_rule;
+  double delta_c, margin, img_tol, s_fac;
 };
 Grid grid_from(const double* g) {
   Grid G;
@@ -113,6 +114,7 @@ Grid grid_from(const double* g) {
   G.n_bins_r = (int)g[3]; G.n_bins_theta = (int)g[4]; G.max_iter = (int)g[5];
   G.uniform = (int)g[6]; G.delta_c = g[7]; G.margin = g[8]; G.img_tol = g[9];
   G.ld_split = (int)g[10];
+  G.grad_rule = (int)g[11]; G.s_fac = g[12];
   return G;
 }
 
@@ -608,14 +610,14 @@ std::vector<Box<T>> build_sectors(const std::vector<Pt<T>>& pts, const Lens<doub
     for (int p : mine) { rlo = std::min(rlo, pts[p].rv); rhi = std::max(rhi, pts[p].rv); }
     double hr = (rhi - rlo) / BR;
     std::vector<int> rb(np, 0), occR(BR, 0);
-    std::vector<uint64_t> tmaskR(BR, 0);
+    std::vector<std::vector<char>> tmaskR(BR, std::vector<char>(BT, 0));  // theta bins per r bin
     for (int p : mine) {
       int b = hr > 0 ? (int)std::floor((pts[p].rv - rlo) / hr) : 0;
       if (b > BR - 1) b = BR - 1;
       if (b < 0) b = 0;
       rb[p] = b;
       occR[b] = 1;
-      tmaskR[b] |= (uint64_t)1 << tb[p];
+      tmaskR[b][tb[p]] = 1;
     }
     // Step 4: fill gaps that an image wraps round.
     std::vector<int> fill(BR, 0);
@@ -623,14 +625,13 @@ std::vector<Box<T>> build_sectors(const std::vector<Pt<T>>& pts, const Lens<doub
       if (occR[b] || !occR[b - 1]) continue;  // b = first empty bin of a gap
       int e = b;
       while (e < BR && !occR[e]) ++e;       // gap = [b, e); bin BR-1 is occupied
-      uint64_t below = 0, above = 0;
-      for (int k = 0; k < b; ++k) below |= tmaskR[k];
-      for (int k = e; k < BR; ++k) above |= tmaskR[k];
-      uint64_t shared = below & above;
+      std::vector<char> below(BT, 0), above(BT, 0);
+      for (int k = 0; k < b; ++k) for (int t = 0; t < BT; ++t) below[t] |= tmaskR[k][t];
+      for (int k = e; k < BR; ++k) for (int t = 0; t < BT; ++t) above[t] |= tmaskR[k][t];
       double rg = rlo + hr * 0.5 * (double)(b + e);
       bool inside = false;
       for (int t = 0; t < BT && !inside; ++t) {
-        if (!((shared >> t) & 1)) continue;
+        if (!(below[t] && above[t])) continue;
         double th = -PI + (t + 0.5) * ht;
         if (maps_inside(Lv, C(rg * std::cos(th), rg * std::sin(th)), wc, rho)) inside = true;
       }
@@ -764,9 +765,18 @@ T crossing(const double* xs, const T* ys, int npt, double x_in, double x_out, co
 }
 
 // f(delta): LD correction (Appendix A.2) or the uniform rule delta + 1/2.
+// The paper's gradient rule (Sec. 3.5, G.grad_rule = 1) keeps the value and
+// gives the LD correction the fixed derivative of its second-order branch,
+// f'(delta) = 2/3, on both branches.
 template <class T>
 T fdelta(const T& delta, const Grid& G) {
   if (G.uniform) return delta + 0.5;
+  if (G.grad_rule) {
+    const double dv_ = val(delta);
+    const double fv = dv_ >= G.delta_c ? (0.5 + dv_) * ((2.0 / 3.0) * std::sqrt(1.0 + 1.0 / (2.0 * dv_)))
+                                       : (2.0 / 3.0) * dv_ + 0.5;
+    return T(fv) + (2.0 / 3.0) * (delta - dv_);  // value fv, tangent (2/3) d delta
+  }
   if (val(delta) >= G.delta_c) return (0.5 + delta) * ((2.0 / 3.0) * sqrt(1.0 + 1.0 / (2.0 * delta)));
   return (2.0 / 3.0) * delta + 0.5;
 }
@@ -831,6 +841,24 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
       chi[l] = val(d[l]) < val(rho);  // chi = Theta(rho - d), strict (Sec. 2.2)
     }
     T row(0.0);
+    if constexpr (std::is_same<T, Dual>::value) {
+      // The paper's gradient rule (Sec. 3.5): the indicator chi = Theta(x)
+      // gets the derivative of a sigmoid of steepness S, dchi/dx =
+      // S s (1 - s), s = 1 / (1 + e^{-S x}).  READING: x = (rho - d) / rho
+      // (S dimensionless); each ray's term I_l dchi_l (the interior weight),
+      // a tangent only -- the primal value is unchanged.
+      if (G.grad_rule) {
+        for (int l = 0; l < NT; ++l) {
+          T x = (rho - d[l]) / rho;
+          double sx = G.s_fac * val(x);
+          if (std::fabs(sx) > 40.0) continue;
+          double sg = 1.0 / (1.0 + std::exp(-sx));
+          double dchi = G.s_fac * sg * (1.0 - sg);
+          double Iv = val(brightness(d[l] * d[l] / rho2, u1, u2, G));
+          row = row + (Iv * dchi) * (x - val(x));
+        }
+      }
+    }
     for (int l = 0; l < NT; ++l) {
       if (!chi[l]) continue;
       auto idx = [&](int k) -> int {  // -1: beyond a non-periodic edge
@@ -1059,6 +1087,11 @@ int orc_limb_points(const double* prm, double t, const double* grid, double* out
 void orc_magnification(const double* prm, int S, const double* t, int E, const double* grid,
                        double* A, uint32_t* status) {
   Grid G = grid_from(grid);
+  // Epochs are independent: the baseline build compiled with OpenMP runs
+  // them on all host cores (the default build is single-threaded).
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+#endif
   for (int s = 0; s < S; ++s)
     for (int e = 0; e < E; ++e) {
       uint32_t st = 0;

@@ -52,12 +52,16 @@ constexpr int NW_MAX = NT_WIDE / 32;  // warps per block, largest instantiation
 constexpr int NW_DER = NT_BASE / 32;  // warps per block, derivative mode
 constexpr int QMAX = 2048;       // work queue
 constexpr int PMAX_MIN = 512;    // FP64-polished image-limb points per epoch (at least)
-constexpr int MAXT = 32;         // theta runs (<= n_bins_theta / 2)
+constexpr int MAXT = 32;         // theta runs (more: ICRS_ST_OVERFLOW)
 constexpr int MAXRB = 32;        // r bins per theta run
 constexpr int MAXCELL = 96;      // (theta run, r run) cells
 constexpr int MAXBOX = 96;       // candidate sectors before merging
 constexpr int MAXANCH = 128;     // FP64 anchors per sector
 constexpr int GTH_MAX = 256;     // columns per theta group (at most)
+// Deferred boundary points per warp in the forward ray stage (8 words each):
+// 32, one per lane; 16 for a triple lens, whose 10 image slots per limb point
+// leave less shared memory for the FP64 point table.
+__host__ __device__ constexpr int dq_entries(int nl) { return nl == 2 ? 32 : 16; }
 constexpr int MAXCELL_D = 32;    // cells with tracked derivatives
 constexpr int MAXBOX_D = 32;     // candidate sectors with tracked derivatives
 constexpr float TINY_EXTENT = 3e-4f;  // images smaller than this x rho skip FP64 decisions
@@ -112,15 +116,15 @@ struct Shared {
   uint32_t status;
   int warm;            // roots[] hold the previous epoch of this set
   int qn, pn;
-  unsigned long long tocc;
+  unsigned long long tocc[2];   // occupied theta bins (up to 128)
   int nT, full;
-  signed char runT[64];
+  signed char runT[128];
   int startT[MAXT];
   unsigned int t_rlo_u[MAXT], t_rhi_l[MAXT];
   unsigned long long t_rlo[MAXT], t_rhi[MAXT];
   double rlo[MAXT], hr[MAXT];
   unsigned int rocc[MAXT];
-  unsigned long long tmask[MAXT][MAXRB];
+  unsigned long long tmask[MAXT][MAXRB][2];  // theta bins of each (run, r bin)
   signed char rrun[MAXT][MAXRB];
   int cellbase[MAXT + 1];
   int ncell;
@@ -491,9 +495,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   // boundary points: forward mode, a deferred queue per warp of 32 points x
   // 8 words (stencil, row factor, indices); derivative mode, the indices of
   // the current row segment's points
-  const bool DEFER = false;
   (void)defer;
-  int* wqueue = (int*)p;         p += sizeof(int) * NW * (!DER ? 256 : 64);
+  int* wqueue = (int*)p;         p += sizeof(int) * NW * (!DER ? 8 * dq_entries(NL) : 64);
   // derivative mode: its state and the per-warp ray seeds
   DerShared& ds = *(DerShared*)p;  p += DER ? sizeof(DerShared) : 0;
   DualD* cdual = ds.cx;
@@ -586,7 +589,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       sh.pn = 0;
       for (int c = 0; c < 16; ++c) sh.cnt[c] = 0;
       sh.clk0 = clock64();
-      sh.tocc = 0ull;
+      sh.tocc[0] = sh.tocc[1] = 0ull;
     }
     __syncthreads();
     const int ll = sh.L.ll;
@@ -945,7 +948,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       else t = (int)floorf((t32[ps] + kPiF) / (float)ht);
       t = min(max(t, 0), BT - 1);
       tb[ps] = (uint8_t)t;
-      atomicOr(&sh.tocc, 1ull << t);
+      atomicOr(&sh.tocc[t >> 6], 1ull << (t & 63));
     }
     __syncthreads();
 
@@ -953,12 +956,12 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     if (diag_cnt && tid == 0) sh.cnt[13] = sh.cnt[0];
     // ------------------------------------------------ 3. theta runs (cyclic)
     if (tid == 0) {
-      unsigned long long occ = sh.tocc;
+      auto occb = [&](int t) -> bool { return (sh.tocc[t >> 6] >> (t & 63)) & 1ull; };
       bool full = true;
-      for (int t = 0; t < BT; ++t) if (!((occ >> t) & 1ull)) full = false;
-      for (int t = 0; t < 64; ++t) sh.runT[t] = -1;
+      for (int t = 0; t < BT; ++t) if (!occb(t)) full = false;
+      for (int t = 0; t < 128; ++t) sh.runT[t] = -1;
       int nT = 0;
-      if (occ == 0ull) {
+      if (!(sh.tocc[0] | sh.tocc[1])) {
         nT = 0;
       } else if (full) {
         for (int t = 0; t < BT; ++t) sh.runT[t] = 0;
@@ -966,12 +969,12 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         nT = 1;
       } else {
         int t0 = 0;
-        while ((occ >> t0) & 1ull) ++t0;
+        while (occb(t0)) ++t0;
         for (int kk = 1; kk <= BT; ++kk) {
           int t = (t0 + kk) % BT;
-          if (!((occ >> t) & 1ull)) continue;
+          if (!occb(t)) continue;
           int prev = (t + BT - 1) % BT;
-          if ((occ >> prev) & 1ull) sh.runT[t] = sh.runT[prev];
+          if (occb(prev)) sh.runT[t] = sh.runT[prev];
           else if (nT < MAXT) { sh.runT[t] = (signed char)nT; sh.startT[nT] = t; ++nT; }
           else { sh.runT[t] = (signed char)(MAXT - 1); atomicOr(&sh.status, ICRS_ST_OVERFLOW); }
         }
@@ -982,7 +985,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         sh.t_rlo_u[T] = 0xffffffffu; sh.t_rhi_l[T] = 0u;
         sh.t_rlo[T] = ~0ull; sh.t_rhi[T] = 0ull;
         sh.rocc[T] = 0u;
-        for (int b = 0; b < MAXRB; ++b) { sh.tmask[T][b] = 0ull; sh.rrun[T][b] = -1; }
+        for (int b = 0; b < MAXRB; ++b) { sh.tmask[T][b][0] = sh.tmask[T][b][1] = 0ull; sh.rrun[T][b] = -1; }
       }
     }
     __syncthreads();
@@ -1069,7 +1072,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       b = min(max(b, 0), BR - 1);
       rb[ps] = (uint8_t)b;
       atomicOr(&sh.rocc[T], 1u << b);
-      atomicOr(&sh.tmask[T][b], 1ull << tb[ps]);
+      atomicOr(&sh.tmask[T][b][tb[ps] >> 6], 1ull << (tb[ps] & 63));
     }
     __syncthreads();
 
@@ -1088,16 +1091,19 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           int e2 = b;
           while (e2 < BR && !((occ >> e2) & 1u)) ++e2;
           if (e2 >= BR) break;
-          unsigned long long below = 0ull, above = 0ull;
-          for (int k = 0; k < b; ++k) below |= sh.tmask[T][k];
-          for (int k = e2; k < BR; ++k) above |= sh.tmask[T][k];
-          unsigned long long shared_ = below & above;
+          unsigned long long shared_[2];
+          for (int h = 0; h < 2; ++h) {
+            unsigned long long below = 0ull, above = 0ull;
+            for (int k = 0; k < b; ++k) below |= sh.tmask[T][k][h];
+            for (int k = e2; k < BR; ++k) above |= sh.tmask[T][k][h];
+            shared_[h] = below & above;
+          }
           double rg = sh.rlo[T] + sh.hr[T] * 0.5 * (double)(b + e2);
           bool hit = false;
           for (int t0 = 0; t0 < BT && !hit; t0 += 32) {
             int t = t0 + lane;
             bool in = false;
-            if (t < BT && ((shared_ >> t) & 1ull)) {
+            if (t < BT && ((shared_[t >> 6] >> (t & 63)) & 1ull)) {
               double th = -kPi + (t + 0.5) * ht;
               float sth, cth;
               sincosf((float)th, &sth, &cth);
@@ -1318,6 +1324,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     const float c1f = g.uniform ? 0.f : (float)((double)I0 * (sh.u1 + 2.0 * sh.u2));
     const float c2f = g.uniform ? 0.f : (float)(-(double)I0 * sh.u2);
     const bool split = g.ld_split && !g.uniform;  // split-profile boundary rule
+    const float sfac = (float)g.s_fac;            // sigmoid steepness of the paper's gradient rule
     float acc_s = 0.f, acc_c = 0.f;  // Kahan sum of this thread
     uint32_t st_local = 0u;
     float* buf = rowbuf + warp * (seg + 4);
@@ -1424,8 +1431,6 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       __syncthreads();
       const float dr32 = sh.dr32;
       const float bxw = (float)(sh.dr64 * sh.dth64);
-      float* dq = (float*)(wqueue + warp * 256);  // deferred boundary points (forward, binary)
-      int dq_n = 0;
       auto wrapl = [&](int l) -> int { return l < 0 ? l + NTH : (l >= NTH ? l - NTH : l); };
       // per-point weights (Appendix A).  Points with both neighbours
       // inside (W = 1) are summed directly; points next to the image
@@ -1530,6 +1535,9 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                 fv = (0.5f + dl) * (2.0f / 3.0f) * sq;
                 fp = (2.0f / 3.0f) * sq - (0.5f + dl) / (6.0f * dl * dl * sq);
               } else { fv = (2.0f / 3.0f) * dl + 0.5f; fp = 2.0f / 3.0f; }
+              // the paper's gradient rule: the fixed derivative of the
+              // second-order branch on both branches
+              if (g.grad_rule && !g.uniform) fp = 2.0f / 3.0f;
               if (isL) fL = fv; else fR = fv;
               const double tt = xd - xsd[0];
               const double slope = dd1 + (2.0 * tt - 1.0) * dd2 + ((3.0 * tt - 6.0) * tt + 2.0) * dd3;
@@ -1589,23 +1597,6 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           if (DER && !(Lin || Rin) && !(fL + fR - 1.0f > 0.f)) sd_n[0] = sd_n[1] = 0, sd_c[0] = sd_c[1] = 0.f;
         return W;
       };
-      // deferred boundary points (forward, binary): one per lane, the term
-      // r_i dr dth I W straight into this thread's compensated sum
-      auto flush_deferred = [&]() {
-        __syncwarp();
-        if (lane < dq_n) {
-          const float* e_ = dq + lane * 8;
-          const float I = brightness(-e_[2]);
-          const float W = boundary_weight(0, e_, __float_as_int(e_[6]), __float_as_int(e_[7]), nullptr);
-          const float term = e_[5] * I * W;
-          const float y = term - acc_c;
-          const float tt = acc_s + y;
-          acc_c = (tt - acc_s) - y;
-          acc_s = tt;
-        }
-        __syncwarp();
-        dq_n = 0;
-      };
       if constexpr (!DER) {
         // ---- forward ray stage.  A warp takes a task of 32 rows (lane = row
         // i) and a chunk [c0, c1) of theta columns, and sweeps the columns in
@@ -1619,7 +1610,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         // points (Appendix A per-point rule).  One warp vote per column covers
         // both rare events: a ray that FP32 cannot decide, and a boundary
         // point to queue.
-        float* dq = (float*)(wqueue + warp * 256);
+        constexpr int DQ = dq_entries(NL);
+        float* dq = (float*)(wqueue + warp * 8 * DQ);
         int dq_n = 0;
         const int CH = sh.chunk;
         const int nch = (NTH + CH - 1) / CH;
@@ -1722,7 +1714,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           auto push = [&](bool isb, int m, float a, float b, float c, float d, float e) {
             const unsigned bm = __ballot_sync(0xffffffffu, isb);
             if (!bm) return;
-            if (dq_n + __popc(bm) > 32) flush_queue();
+            if (dq_n + __popc(bm) > DQ) flush_queue();
             if (isb) {
               float* e_ = dq + (dq_n + __popc(bm & lt_mask)) * 8;
               const float v5[5] = {a, b, c, d, e};
@@ -1947,6 +1939,21 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             bool inside = false, edge = false;
             if (mi < cnt - 2) {
               float v = buf[mi];
+              if (DER && g.grad_rule && !isinf(v)) {
+                // the paper's gradient rule (Sec. 3.5): the indicator chi =
+                // Theta(x), x = (rho - d) / rho, gets the sigmoid derivative
+                // S s (1 - s), s = 1 / (1 + e^{-S x}), with the interior
+                // weight: seed -I S s (1 - s) / rho on d, and I S s (1 - s)
+                // d / rho^2 on rho (tangents only)
+                const float dd_ = sqrtf(fabsf(v));
+                const float sx = sfac * (1.0f - dd_ / rho32);
+                if (fabsf(sx) < 40.0f) {
+                  const float sg = 1.0f / (1.0f + __expf(-sx));
+                  const float c = brightness(fabsf(v)) * sfac * sg * (1.0f - sg);
+                  atomicAdd(&ab[mi], -c / rho32);
+                  pg[5] += c * dd_ / (rho32 * rho32);
+                }
+              }
               inside = signbit(v);
               if (inside) {
                 bool Lin = signbit(buf[mi - 1]), Rin = signbit(buf[mi + 1]);
@@ -1966,19 +1973,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               }
             }
             unsigned msk = __ballot_sync(0xffffffffu, edge);
-            if (DEFER && msk) {
-              // keep the point's stencil, row factor and indices; solve 32 at
-              // a time (one per lane) when the queue would overflow
-              if (dq_n + __popc(msk) > 32) { flush_deferred(); }
-              if (edge) {
-                float* e_ = dq + (dq_n + __popc(msk & ((1u << lane) - 1u))) * 8;
-                for (int k = 0; k < 5; ++k) e_[k] = buf[mi - 2 + k];
-                e_[5] = ri * bxw;
-                e_[6] = __int_as_float(lo + mi);
-                e_[7] = __int_as_float(i);
-              }
-              dq_n += __popc(msk);
-            } else if (msk) {
+            if (msk) {
               int pos = nq + __popc(msk & ((1u << lane) - 1u));
               if (edge) {
                 if (pos < 64) wq[pos] = mi;
@@ -2087,7 +2082,6 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         acc_c = (tt - acc_s) - y;
         acc_s = tt;
       }
-      if (DEFER) flush_deferred();
       }  // DER row loop
       __syncthreads();
       if (DER && tid < 12) {
@@ -2259,7 +2253,7 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
   const int NW = nt / 32;
   (void)defer;
-  b += sizeof(int) * NW * (!der ? 256 : 64);  // per-warp boundary queues
+  b += sizeof(int) * NW * (!der ? 8 * dq_entries(NL) : 64);  // per-warp boundary queues
   const int seg = row_segment(g.n_theta, der);
   if (der) b += sizeof(DerShared) + 2 * sizeof(float) * NW * (seg + 4);  // state, row buffers and ray seeds
   b += sizeof(cf) * (GTH_MAX + 2);
@@ -2273,10 +2267,12 @@ static int check_grid(const icrs_grid* g) {
   if (g->n_theta < 8 || g->n_theta > 8192) return ICRS_EINVAL;
   if (g->n_limb < 16 || g->n_limb > 1024) return ICRS_EINVAL;
   if (g->n_bins_r < 2 || g->n_bins_r > MAXRB) return ICRS_EINVAL;
-  if (g->n_bins_theta < 2 || g->n_bins_theta > 64) return ICRS_EINVAL;
+  if (g->n_bins_theta < 2 || g->n_bins_theta > 128) return ICRS_EINVAL;
   if (!(g->delta_c > 0.0) || !(g->margin >= 0.0) || !(g->img_tol > 0.0)) return ICRS_EINVAL;
   if (g->max_iter < 1 || g->max_iter > 10000) return ICRS_EINVAL;
   if (g->ld_split != 0 && g->ld_split != 1) return ICRS_EINVAL;
+  if (g->grad_rule != 0 && g->grad_rule != 1) return ICRS_EINVAL;
+  if (g->grad_rule && !(g->s_fac > 0.0)) return ICRS_EINVAL;
   return ICRS_OK;
 }
 
@@ -2350,8 +2346,15 @@ static int launch_inst(const icrs_params* p, int S, const double* t, int E, cons
   if (!fits(pmax, 0, defer)) return ICRS_EUNSUPPORTED;
   int has_plo = (DER && fits(pmax, 1, defer)) ? 1 : 0;
   const int np_all = g->n_limb * (NL * NL + 1);
-  while (pmax < np_all && fits(pmax * 2 < np_all ? pmax * 2 : np_all, has_plo, defer))
-    pmax = pmax * 2 < np_all ? pmax * 2 : np_all;
+  // the FP64 point table takes the remaining room (16 bytes per entry), up to
+  // one entry per image-limb slot
+  {
+    const size_t used = mag_smem_bytes(NL, *g, 0, has_plo, DER, defer, nt) + sizeof(Shared);
+    const size_t room = used < (size_t)optin ? (size_t)optin - used : 0;
+    const size_t cap = room / (2 * sizeof(double));
+    pmax = (int)(cap < (size_t)np_all ? cap : (size_t)np_all);
+    if (pmax < PMAX_MIN) pmax = PMAX_MIN;
+  }
   if (!DER) has_plo = fits(pmax, 1, defer) ? 1 : 0;
   const size_t smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER, defer, nt);
   if constexpr (mag_threads(NL, DER) != NT_BASE) {
@@ -2412,9 +2415,10 @@ void icrs_grid_default(icrs_grid* g) {
   if (!g) return;
   memset(g, 0, sizeof(*g));
   g->n_r = 64; g->n_theta = 256; g->n_limb = 500;
-  g->n_bins_r = 32; g->n_bins_theta = 64; g->max_iter = 100; g->uniform = 0;
+  g->n_bins_r = 32; g->n_bins_theta = 128; g->max_iter = 100; g->uniform = 0;
   g->n_lens = 2;
   g->delta_c = 0.02; g->margin = 0.05; g->img_tol = 1e-3;
+  g->s_fac = 100.0;
 }
 
 const char* icrs_strerror(int code) {

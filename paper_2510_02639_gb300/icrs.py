@@ -53,7 +53,7 @@ class IcrsGrid(ctypes.Structure):
                 ("n_bins_r", ctypes.c_int32), ("n_bins_theta", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("uniform", ctypes.c_int32), ("n_lens", ctypes.c_int32),
                 ("delta_c", ctypes.c_double), ("margin", ctypes.c_double), ("img_tol", ctypes.c_double),
-                ("ld_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ld_split", ctypes.c_int32), ("grad_rule", ctypes.c_int32), ("s_fac", ctypes.c_double)]
 
 
 PARAMS_DTYPE = np.dtype([("t0", "<f8"), ("tE", "<f8"), ("u0", "<f8"), ("alpha", "<f8"),
@@ -231,7 +231,8 @@ def grid_from_dict(d: dict, n_lens: int = 2) -> IcrsGrid:
                      n_bins_r=int(d["n_bins_r"]), n_bins_theta=int(d["n_bins_theta"]),
                      max_iter=int(d["max_iter"]), uniform=int(d["uniform"]), n_lens=int(n_lens),
                      delta_c=float(d["delta_c"]), margin=float(d["margin"]),
-                     img_tol=float(d["img_tol"]), ld_split=int(d.get("ld_split", 0)))
+                     img_tol=float(d["img_tol"]), ld_split=int(d.get("ld_split", 0)),
+                     grad_rule=int(d.get("grad_rule", 0)), s_fac=float(d.get("s_fac", 100.0)))
 
 
 def magnification_vjp(params_dev, t, grid: IcrsGrid, gA, per_epoch=False, stream=None):

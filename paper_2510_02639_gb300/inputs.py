@@ -13,8 +13,9 @@ import numpy as np
 
 # Default grid (Sec. 3.2-3.3: N_limb ~ 500; polar grid N_r x N_theta per sector).
 DEFAULT_GRID = dict(
-    n_r=64, n_theta=256, n_limb=500, n_bins_r=32, n_bins_theta=64,
+    n_r=64, n_theta=256, n_limb=500, n_bins_r=32, n_bins_theta=128,
     max_iter=100, uniform=0, delta_c=0.02, margin=0.05, img_tol=1e-3, ld_split=0,
+    grad_rule=0, s_fac=100.0,
 )
 
 

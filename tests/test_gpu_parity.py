@@ -248,3 +248,88 @@ def test_quadratic_limb_darkening_and_split_rule(G, oracle_mod):
     tt = torch.tensor(t, device="cuda")
     with pytest.raises(G.IcrsError):
         G.magnification_vjp(pd, tt, G.grid_from_dict(I.grid(ld_split=1), 2), torch.ones_like(tt))
+
+
+def test_qualification_sample_at_headline_grid(G):
+    """The 512-epoch qualification sample of the batch (peak epochs, random
+    epochs, small sources at moderate magnification, sources inside a
+    caustic; tests/golden/batch_qualification.json, written by a script that
+    calls only the oracle) at the headline grid, one launch with one set per
+    epoch (cold roots): every epoch against the stored oracle value on the
+    same grid at 1e-5."""
+    import json
+    import os
+    import torch
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "batch_qualification.json")
+    gold = json.load(open(path))
+    params, t = I.binary_batch()
+    rows = gold["epochs"]
+    g = I.grid(**gold["grids"][0])
+    ps = [params[r["set"]] for r in rows]
+    tt = np.array([[t[r["set"], r["epoch"]]] for r in rows])
+    A, st = run_gpu(G, ps, tt, g)
+    Ao = np.array([[r["A"][0]] for r in rows])
+    so = np.array([[r["status"][0]] for r in rows])
+    assert_parity(A, Ao, what="qualification sample")
+    assert_status(st, so, what="qualification sample")
+
+
+def test_triple_at_qualified_grid(G):
+    """The triple-lens curve (rho = 5e-4) at 1024 x 2048 with N_limb = 500 (it
+    fits in shared memory since the per-sector offset table holds at most
+    256 columns): 32 epochs (the 16 of highest point-source magnification and
+    16 spread along the curve, tests/golden/triple_qualification.json) in one
+    launch, each against the stored oracle value on the same grid at 1e-5,
+    and within 1e-4 of the oracle at 4096 x 8192 up to that reference's own
+    Richardson bound."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "triple_qualification.json")
+    gold = json.load(open(path))
+    params, t = I.triple_curve()
+    rows = gold["epochs"]
+    g = I.grid(**gold["grids"][0])
+    tt = np.array([[t[0, r["epoch"]] for r in rows]])
+    A, st = run_gpu(G, params, tt, g)
+    Ao = np.array([[r["A"][0] for r in rows]])
+    so = np.array([[r["status"][0] for r in rows]])
+    assert_parity(A, Ao, what="triple at 1024 x 2048")
+    assert_status(st, so, what="triple at 1024 x 2048")
+    ref = np.array([r["A"][-1] for r in rows])
+    bound = np.abs(np.array([r["A"][-1] / r["A"][-2] - 1.0 for r in rows]))
+    err = np.abs(A[0] / ref - 1.0)
+    assert np.all(err <= 1e-4 + bound), (err.max(), bound[err.argmax()])
+
+
+@pytest.mark.parametrize("q", [1e-5, 1e-3, 1e-1])
+def test_root_stage_error_of_fp32_coefficients(G, oracle_mod, q):
+    """The root stage forms the polynomial coefficients in FP32 (about the
+    lightest lens) and refines each image by a double-float Newton step, with
+    FP64 fallbacks.  Its image-limb points (r, theta) against the oracle's
+    FP64 ones, for a source crossing the central caustic (8 epochs, 500 limb
+    points each): same image count at every limb point, and positions equal
+    to the FP32 rounding of the FP64 values (relative 2^-23) -- the sector
+    bounds are then taken from FP64-polished or double-float values."""
+    import torch
+    p = I.binary(q=q, s=1.0, rho=1e-3, u0=0.0, alpha=0.3, t0=0.0, tE=20.0)
+    t = np.linspace(-0.03, 0.03, 8)
+    g = I.grid()
+    pd = G.params_to_device([p])
+    tt = torch.tensor(t[None, :], device="cuda")
+    _, _, _, _, pts = G.magnification_diag(pd, tt, G.grid_from_dict(g, 2), points=True)
+    pts = pts.cpu().numpy()[0]
+    worst = 0.0
+    for e in range(len(t)):
+        lp = oracle_mod.limb_points(p, t[e], g)          # [N_limb, 5, (r, theta, valid)]
+        gp = pts[e].reshape(lp.shape[0], 5, 4)
+        for k in range(lp.shape[0]):
+            vo = lp[k][lp[k, :, 2] > 0][:, :2]
+            vg = gp[k][(gp[k, :, 2].astype(int) & 1) > 0][:, :2].astype(np.float64)
+            assert len(vo) == len(vg), (e, k, len(vo), len(vg))
+            zo = vo[:, 0] * np.exp(1j * vo[:, 1])
+            zg = vg[:, 0] * np.exp(1j * vg[:, 1])
+            for z in zo:
+                d = np.min(np.abs(zg - z)) / max(1.0, abs(z))
+                worst = max(worst, d)
+    print(f"q={q}: worst image-limb point error {worst:.2e} (relative to max(1, |z|))")
+    assert worst <= 4 * 2.0 ** -23

@@ -304,3 +304,48 @@ def test_forward_mode_matches_fd(oracle_mod):
             agreed += abs(dA[0, e, i] - fd[0][e]) <= 5e-5 * scale
     assert compared >= 40
     assert agreed == compared
+
+
+def test_image_tolerance_convention_does_not_change_results(oracle_mod):
+    """img_tol is a convention: true images have FP64 residuals ~1e-15 and the
+    polynomial's spurious roots residuals ~1e-2 or more, so img_tol = 1e-3
+    (the default) and 1e-5 classify every root alike and give the same
+    magnifications and status on caustic-crossing epochs and on random
+    epochs of the batch (q down to 1e-5)."""
+    params, t = I.caustic_crossing_binary(n_epochs=40)
+    bparams, bt = I.binary_batch()
+    rng = np.random.default_rng(17)
+    picks = [(int(rng.integers(64)), int(rng.integers(10000))) for _ in range(24)]
+    cases = [(params[0], t[0, i]) for i in range(40)] + [(bparams[s], bt[s, e]) for s, e in picks]
+    for p, tt in cases:
+        A3, s3 = oracle_mod.magnification(p, [tt], I.grid(img_tol=1e-3))
+        A5, s5 = oracle_mod.magnification(p, [tt], I.grid(img_tol=1e-5))
+        assert A3[0, 0] == pytest.approx(A5[0, 0], rel=1e-12), (p, tt)
+        assert s3[0, 0] == s5[0, 0]
+
+
+def test_paper_gradient_rules_change_tangents_only(oracle_mod):
+    """The paper's gradient rules (grad_rule = 1: sigmoid indicator
+    derivative of steepness S, fixed f'(delta) = 2/3) leave the magnification
+    bitwise unchanged; for a uniform source (f_U' = 1 already) with S -> 0 the
+    sigmoid term vanishes linearly in S, so the derivative tends to the exact
+    one; for limb darkening the fixed f' changes the boundary terms."""
+    params, t = I.caustic_crossing_binary()
+    ts = t[:, 200:260:10]
+    gu = I.grid(uniform=1)
+    A0, d0, _ = oracle_mod.magnification_fwd(params, ts, gu)
+    for S in (1e-3, 2e-3):
+        A1, d1, _ = oracle_mod.magnification_fwd(params, ts, dict(gu, grad_rule=1, s_fac=S))
+        assert np.array_equal(A0, A1)
+        diff = d1 - d0
+        if S == 1e-3:
+            ref = diff
+        else:
+            # linear in S: doubling S doubles the sigmoid term
+            np.testing.assert_allclose(diff, 2.0 * ref, rtol=1e-6, atol=1e-12 * np.abs(d0).max())
+            assert np.abs(diff).max() <= 1e-2 * np.abs(d0).max()
+    gl = I.grid()
+    A2, d2, _ = oracle_mod.magnification_fwd(params, ts, gl)
+    A3, d3, _ = oracle_mod.magnification_fwd(params, ts, dict(gl, grad_rule=1, s_fac=1e-9))
+    assert np.array_equal(A2, A3)
+    assert np.abs(d3 - d2).max() > 1e-3 * np.abs(d2).max()   # the fixed f' matters
