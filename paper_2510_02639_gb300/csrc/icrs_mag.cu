@@ -934,10 +934,16 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     // ------------------------------------------------ 2. theta bins
     for (int ps = tid; ps < NP; ps += NT) {
       if (!(meta[ps] & M_VALID) || (meta[ps] & M_EXACT)) continue;
+      // distance of the FP32 angle from the nearest bin edge, against the
+      // error of that FP32 evaluation: the point's own bound e32 / r, atan2f
+      // (<= 2 ulp of pi, 4.8e-7), the float pi (8.7e-8), the sum (2.4e-7),
+      // and the division by the float bin width (<= 128 bins x 1.2e-7 bin
+      // widths, 7.5e-7 rad): 1.6e-6 rad in all; 64 EPS32 = 3.8e-6 leaves a
+      // factor of two.  Closer points get an FP64 angle.
       float u = (t32[ps] + kPiF) / (float)ht;
       float fr = u - floorf(u);
       float d = fminf(fr, 1.0f - fr) * (float)ht;
-      float eth = e32[ps] / fmaxf(r32[ps], 1e-30f) + 4.0f * EPS32 * 4.0f;
+      float eth = e32[ps] / fmaxf(r32[ps], 1e-30f) + 64.0f * EPS32;
       if (d <= eth) q_push(sh, queue, ps);
     }
     run_polish();
@@ -1173,10 +1179,14 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       int c = sh.cellbase[T] + sh.rrun[T][rb[ps]];
       return c < MAXCELL ? c : MAXCELL - 1;
     };
+    // A point lies past the wrap of its angular interval when its bin comes
+    // before the interval's first bin.  The decision is taken on the bin, not
+    // on the angle: a point binned in FP64 next to the interval's first edge
+    // can have an FP32 angle on the other side of that edge, and the FP32
+    // candidate pass and the FP64 extreme pass must unwrap it alike.
     auto unwrap_t = [&](int ps, double th) -> double {
       int T = sh.runT[tb[ps]];
-      double start = -kPi + sh.startT[T] * ht;
-      return th < start ? th + 2.0 * kPi : th;
+      return (int)tb[ps] < sh.startT[T] ? th + 2.0 * kPi : th;
     };
     for (int ps = tid; ps < NP; ps += NT) {
       if (!(meta[ps] & M_VALID)) continue;
@@ -1712,20 +1722,35 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           // queue boundary point m = l - 2 with its stencil (v[m-2..m+2]) =
           // (a, b, c, d, e), the inside flags at bits 4..0 of win
           auto push = [&](bool isb, int m, float a, float b, float c, float d, float e) {
-            const unsigned bm = __ballot_sync(0xffffffffu, isb);
-            if (!bm) return;
-            if (dq_n + __popc(bm) > DQ) flush_queue();
-            if (isb) {
-              float* e_ = dq + (dq_n + __popc(bm & lt_mask)) * 8;
-              const float v5[5] = {a, b, c, d, e};
+            unsigned rem = __ballot_sync(0xffffffffu, isb);
+            // up to 32 points, the queue holds DQ: take the lowest set lanes
+            // that fit, flushing whenever the queue is full (warp-uniform)
+            while (rem) {
+              if (dq_n == DQ) flush_queue();
+              unsigned take = rem;
+              const int room = DQ - dq_n;
+              if (__popc(take) > room) {
+                take = 0u;
+                unsigned r = rem;
+                for (int k = 0; k < room; ++k) {
+                  const unsigned low = r & (0u - r);
+                  take |= low;
+                  r ^= low;
+                }
+              }
+              if (take & (1u << lane)) {
+                float* e_ = dq + (dq_n + __popc(take & lt_mask)) * 8;
+                const float v5[5] = {a, b, c, d, e};
 #pragma unroll
-              for (int k = 0; k < 5; ++k)
-                e_[k] = __int_as_float(__float_as_int(v5[k]) | (((win >> (4 - k)) & 1u) << 31));
-              e_[5] = ri * bxw;
-              e_[6] = __int_as_float(m);
-              e_[7] = __int_as_float(i);
+                for (int k = 0; k < 5; ++k)
+                  e_[k] = __int_as_float(__float_as_int(v5[k]) | (((win >> (4 - k)) & 1u) << 31));
+                e_[5] = ri * bxw;
+                e_[6] = __int_as_float(m);
+                e_[7] = __int_as_float(i);
+              }
+              dq_n += __popc(take);
+              rem &= ~take;
             }
-            dq_n += __popc(bm);
           };
           // main column l (inside [c0, c1), no wrap; the group already
           // loaded): ring (a, b, c, d) = v[l-4..l-1], result into dst.  The

@@ -165,6 +165,34 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _need(x, dtype, shape=None, name="tensor"):
+    """Raise ValueError unless x is a contiguous CUDA tensor of dtype (and shape)."""
+    if x is None or not x.is_cuda or x.dtype != dtype or not x.is_contiguous():
+        got = None if x is None else (x.dtype, x.device, x.is_contiguous())
+        raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor, got {got}")
+    if shape is not None and tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name}: need shape {tuple(shape)}, got {tuple(x.shape)}")
+    return x
+
+
+def _nsets(params_dev):
+    """Number of icrs_params structs in a uint8 device tensor."""
+    import torch
+    _need(params_dev, torch.uint8, name="params")
+    if params_dev.numel() % PARAMS_DTYPE.itemsize:
+        raise ValueError("params: size is not a multiple of sizeof(icrs_params)")
+    return params_dev.numel() // PARAMS_DTYPE.itemsize
+
+
+def _times(t, S):
+    """t: [S, E] float64 CUDA tensor; returns E."""
+    import torch
+    if t.dim() != 2 or t.shape[0] != S:
+        raise ValueError(f"t: need shape [{S}, E], got {tuple(t.shape)}")
+    _need(t, torch.float64, name="t")
+    return t.shape[1]
+
+
 def _stream(torch, stream):
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -181,13 +209,16 @@ def magnification(params_dev, t, grid: IcrsGrid, out=None, status=None, stream=N
     """Finite-source magnification.  params_dev: uint8 device tensor holding S
     icrs_params structs; t: [S, E] float64 device tensor.  Returns (A, status)."""
     import torch
-    S = params_dev.numel() // PARAMS_DTYPE.itemsize
-    assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
-    E = t.shape[-1] if t.dim() > 0 else 0
+    S = _nsets(params_dev)
+    E = _times(t, S)
     if out is None:
         out = torch.empty((S, E), dtype=torch.float64, device=t.device)
+    else:
+        _need(out, torch.float64, (S, E), "out")
     if status is None:
         status = torch.empty((S, E), dtype=torch.int32, device=t.device)
+    else:
+        _need(status, torch.int32, (S, E), "status")
     check(lib.icrs_magnification(_ptr(params_dev), S, _ptr(t), E, ctypes.byref(grid),
                                  _ptr(out), _ptr(status), _stream(torch, stream)))
     return out, status
@@ -197,8 +228,8 @@ def magnification_diag(params_dev, t, grid: IcrsGrid, points=False, stream=None)
     """As magnification(), plus sectors [S, E, 10, 5], counters [S, E, 16] and
     optionally the image-limb points [S, E, N_limb * N_deg, 4] per epoch."""
     import torch
-    S = params_dev.numel() // PARAMS_DTYPE.itemsize
-    E = t.shape[-1]
+    S = _nsets(params_dev)
+    E = _times(t, S)
     out = torch.empty((S, E), dtype=torch.float64, device=t.device)
     status = torch.empty((S, E), dtype=torch.int32, device=t.device)
     sect = torch.empty((S, E, 10, 5), dtype=torch.float64, device=t.device)
@@ -214,7 +245,10 @@ def point_source(params_dev, w, grid: IcrsGrid, n_lens=2, stream=None):
     """Point-source magnification at positions w: [S, n, 2] float64 device.
     Returns (A [S, n], images [S, n, N_deg, 2], n_img [S, n], status [S, n])."""
     import torch
-    S = params_dev.numel() // PARAMS_DTYPE.itemsize
+    S = _nsets(params_dev)
+    if w.dim() != 3 or w.shape[0] != S or w.shape[2] != 2:
+        raise ValueError(f"w: need shape [{S}, n, 2], got {tuple(w.shape)}")
+    _need(w, torch.float64, name="w")
     n = w.shape[1]
     nd = 5 if n_lens == 2 else 10
     A = torch.empty((S, n), dtype=torch.float64, device=w.device)
@@ -240,10 +274,9 @@ def magnification_vjp(params_dev, t, grid: IcrsGrid, gA, per_epoch=False, stream
     of PARAM_ORDER.  Returns (grad [S, 8], dA [S, E, 8] or None, A [S, E],
     status [S, E])."""
     import torch
-    S = params_dev.numel() // PARAMS_DTYPE.itemsize
-    E = t.shape[-1]
-    assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
-    assert gA.dtype == torch.float64 and gA.is_contiguous() and tuple(gA.shape) == (S, E)
+    S = _nsets(params_dev)
+    E = _times(t, S)
+    _need(gA, torch.float64, (S, E), "gA")
     grad = torch.empty((S, 8), dtype=torch.float64, device=t.device)
     dA = torch.empty((S, E, 8), dtype=torch.float64, device=t.device) if per_epoch else None
     A = torch.empty((S, E), dtype=torch.float64, device=t.device)
@@ -258,10 +291,10 @@ def chi2_grad(params_dev, t, grid: IcrsGrid, y, sigma, stream=None):
     parameters of PARAM_ORDER.  Returns (chi2 [S], grad [S, 8], A [S, E],
     status [S, E])."""
     import torch
-    S = params_dev.numel() // PARAMS_DTYPE.itemsize
-    E = t.shape[-1]
-    for x in (t, y, sigma):
-        assert x.dtype == torch.float64 and x.is_cuda and x.is_contiguous() and tuple(x.shape) == (S, E)
+    S = _nsets(params_dev)
+    E = _times(t, S)
+    _need(y, torch.float64, (S, E), "y")
+    _need(sigma, torch.float64, (S, E), "sigma")
     chi2 = torch.empty((S,), dtype=torch.float64, device=t.device)
     grad = torch.empty((S, 8), dtype=torch.float64, device=t.device)
     A = torch.empty((S, E), dtype=torch.float64, device=t.device)
@@ -277,11 +310,11 @@ def marginal_nll_grad(params_dev, t, grid: IcrsGrid, F, sigma, prior, grad=True,
     lambda_S, lambda_base).  Returns (nll [S], grad [S, 8] or None,
     fluxes [S, 2], A [S, E], status [S, E])."""
     import torch
-    S = params_dev.numel() // PARAMS_DTYPE.itemsize
-    E = t.shape[-1]
-    for x in (t, F, sigma):
-        assert x.dtype == torch.float64 and x.is_cuda and x.is_contiguous() and tuple(x.shape) == (S, E)
-    assert prior.dtype == torch.float64 and prior.is_contiguous() and tuple(prior.shape) == (S, 4)
+    S = _nsets(params_dev)
+    E = _times(t, S)
+    _need(F, torch.float64, (S, E), "F")
+    _need(sigma, torch.float64, (S, E), "sigma")
+    _need(prior, torch.float64, (S, 4), "prior")
     nll = torch.empty((S,), dtype=torch.float64, device=t.device)
     g = torch.empty((S, 8), dtype=torch.float64, device=t.device) if grad else None
     fl = torch.empty((S, 2), dtype=torch.float64, device=t.device)
@@ -353,9 +386,18 @@ def magnification_indexed(params_dev, t, grid: IcrsGrid, items, n, A, status=Non
     """ICRS on items[0:n] (indices s * E + e) of the [S, E] problem; writes
     A[s, e] (and status) for those items only."""
     import torch
-    S = params_dev.numel() // PARAMS_DTYPE.itemsize
-    E = t.shape[-1]
-    assert items.dtype == torch.int32 and A.dtype == torch.float64
+    S = _nsets(params_dev)
+    E = _times(t, S)
+    _need(items, torch.int32, name="items")
+    if not 0 <= int(n) <= items.numel():
+        raise ValueError("items: n out of range")
+    _need(A, torch.float64, name="A")
+    if A.numel() != S * E:
+        raise ValueError("A: need S * E values")
+    if status is not None:
+        _need(status, torch.int32, name="status")
+        if status.numel() != S * E:
+            raise ValueError("status: need S * E values")
     check(lib.icrs_magnification_indexed(_ptr(params_dev), S, _ptr(t), E, _ptr(items), int(n), ctypes.byref(grid),
                                          _ptr(A), _ptr(status), _stream(torch, stream)))
     return A
@@ -373,7 +415,7 @@ def mlp_infer(pack, theta, feat, out=None, err=None, stream=None):
     """feat [n, 8] float32 -> (mu, s) [n, 2] float32."""
     import torch
     n = feat.shape[0]
-    assert feat.dtype == torch.float32 and feat.is_contiguous() and feat.shape[1] == 8
+    _need(feat, torch.float32, (n, 8), "feat")
     if out is None:
         out = torch.empty((n, 2), dtype=torch.float32, device=feat.device)
     check(lib.icrs_mlp_infer(_ptr(pack), _ptr(theta), _ptr(feat), n, _ptr(out), _ptr(err), _stream(torch, stream)))
@@ -392,7 +434,10 @@ def mlp_train_step(theta, m, v, pack, step, lr, feat, target, workspace=None, gr
     (grad/loss may be None when not requested)."""
     import torch
     n = feat.shape[0]
-    assert feat.dtype == torch.float32 and target.dtype == torch.float32 and feat.is_contiguous()
+    _need(feat, torch.float32, (n, 8), "feat")
+    _need(target, torch.float32, name="target")
+    if target.numel() != n:
+        raise ValueError("target: need one value per feature row")
     if workspace is None:
         workspace = mlp_workspace(n, feat.device)
     check(lib.icrs_mlp_train_step(_ptr(theta), _ptr(m), _ptr(v), _ptr(pack), int(step), float(lr), _ptr(feat),
@@ -404,8 +449,8 @@ def mlp_train_step(theta, m, v, pack, step, lr, feat, target, workspace=None, gr
 def surrogate_features(params_dev, t, grid: IcrsGrid, stream=None):
     """Returns (features [S*E, 8] f32, A_ps [S*E] f64, status [S*E] int32)."""
     import torch
-    S = params_dev.numel() // PARAMS_DTYPE.itemsize
-    E = t.shape[-1]
+    S = _nsets(params_dev)
+    E = _times(t, S)
     feat = torch.empty((S * E, 8), dtype=torch.float32, device=t.device)
     Aps = torch.empty((S * E,), dtype=torch.float64, device=t.device)
     st = torch.empty((S * E,), dtype=torch.int32, device=t.device)
@@ -439,7 +484,10 @@ def mlp_train_step_noalloc(theta, m, v, pack, step, lr, feat, target, grad=None,
     overlapping calls on one device race on that scratch."""
     import torch
     n = feat.shape[0]
-    assert feat.dtype == torch.float32 and target.dtype == torch.float32 and feat.is_contiguous()
+    _need(feat, torch.float32, (n, 8), "feat")
+    _need(target, torch.float32, name="target")
+    if target.numel() != n:
+        raise ValueError("target: need one value per feature row")
     check(lib.icrs_mlp_train_step_noalloc(_ptr(theta), _ptr(m), _ptr(v), _ptr(pack), int(step), float(lr),
                                           _ptr(feat), _ptr(target), n, _ptr(grad), _ptr(loss), _ptr(err),
                                           _stream(torch, stream)))
@@ -469,7 +517,9 @@ def surrogate_target(A, A_ps, feat, out=None, stream=None):
     """target [n] float32 = 1e4 log(A / A_ps) - feat[:, 7] (icrs_surrogate_target)."""
     import torch
     n = A.numel()
-    assert A.dtype == torch.float64 and A_ps.dtype == torch.float64 and feat.dtype == torch.float32
+    _need(A, torch.float64, name="A")
+    _need(A_ps, torch.float64, (n,), "A_ps")
+    _need(feat, torch.float32, (n, 8), "feat")
     if out is None:
         out = torch.empty((n,), dtype=torch.float32, device=A.device)
     check(lib.icrs_surrogate_target(_ptr(A), _ptr(A_ps), _ptr(feat), n, _ptr(out), _stream(torch, stream)))
@@ -480,7 +530,11 @@ def surrogate_batch(feat, target, idx, out_feat=None, out_target=None, stream=No
     """Rows idx of (feat [N, 8], target [N]) into (out_feat [n, 8], out_target [n])."""
     import torch
     n = idx.numel()
-    assert idx.dtype == torch.int32 and feat.is_contiguous()
+    _need(idx, torch.int32, name="idx")
+    _need(feat, torch.float32, name="feat")
+    _need(target, torch.float32, name="target")
+    if feat.dim() != 2 or feat.shape[1] != 8 or target.numel() != feat.shape[0]:
+        raise ValueError("feat / target: need [N, 8] and [N]")
     if out_feat is None:
         out_feat = torch.empty((n, 8), dtype=torch.float32, device=feat.device)
     if out_target is None:

@@ -274,6 +274,30 @@ def test_qualification_sample_at_headline_grid(G):
     assert_status(st, so, what="qualification sample")
 
 
+def test_interval_first_edge_epochs(G):
+    """Five epochs of the 5000 x 2000 scoring batch whose lowest image angle
+    lies within 1e-7 rad above the first edge of its angular interval
+    (tests/golden/interval_edge_epochs.json, written by a script that calls
+    only the oracle and checks that property): the FP32 angle of that point
+    can fall below the edge while its FP64 angle bins it inside, and the
+    sector must still span the whole image.  Each epoch against the stored
+    oracle value at 1e-5 with the same status bits."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "interval_edge_epochs.json")
+    gold = json.load(open(path))
+    params, t = I.binary_batch(**gold["batch"])
+    rows = gold["epochs"]
+    g = I.grid(**gold["grid"])
+    ps = [params[r["set"]] for r in rows]
+    tt = np.array([[t[r["set"], r["epoch"]]] for r in rows])
+    A, st = run_gpu(G, ps, tt, g)
+    Ao = np.array([[r["A"]] for r in rows])
+    so = np.array([[r["status"]] for r in rows])
+    assert_parity(A, Ao, what="interval first-edge epochs")
+    assert_status(st, so, what="interval first-edge epochs")
+
+
 def test_triple_at_qualified_grid(G):
     """The triple-lens curve (rho = 5e-4) at 1024 x 2048 with N_limb = 500 (it
     fits in shared memory since the per-sector offset table holds at most

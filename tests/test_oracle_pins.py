@@ -276,6 +276,31 @@ def test_sectors_cover_all_images(oracle_mod):
         assert np.all(cov[inside])
 
 
+def test_sectors_cover_images_next_to_an_interval_edge(oracle_mod):
+    """The epochs of tests/golden/interval_edge_epochs.json, whose lowest image
+    angle sits within 1e-7 rad above a theta-bin edge that starts an angular
+    interval: every valid image-limb point lies inside one of the oracle's
+    sectors (a sector built from a subset of its image's points would leave
+    the image's far end outside)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "interval_edge_epochs.json")
+    gold = json.load(open(path))
+    params, t = I.binary_batch(**gold["batch"])
+    g = I.grid(**gold["grid"])
+    for row in gold["epochs"]:
+        p, tt = params[row["set"]], float(t[row["set"], row["epoch"]])
+        boxes, _ = oracle_mod.sectors(p, tt, g)
+        lp = oracle_mod.limb_points(p, tt, g)
+        v = lp[..., 2] > 0
+        R, TH = lp[..., 0][v], lp[..., 1][v]
+        cov = np.zeros(R.shape, bool)
+        for (rlo, rhi, tlo, wd, per) in boxes:
+            d = np.mod(TH - tlo, 2 * np.pi)
+            cov |= (R >= rlo) & (R <= rhi) & ((d <= wd) if not per else True)
+        assert np.all(cov), (row["set"], row["epoch"], int((~cov).sum()))
+
+
 def test_forward_mode_matches_fd(oracle_mod):
     """(vii) The oracle's 8-direction forward-mode derivative equals central
     finite differences of its own primal.  The primal is piecewise smooth
