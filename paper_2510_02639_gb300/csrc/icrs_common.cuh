@@ -34,6 +34,20 @@ template <class T> __device__ __forceinline__ T abs2(cx<T> a) { return fma(a.x, 
 template <class T> __device__ __forceinline__ cx<T> inv(cx<T> a) { T n = T(1) / abs2(a); return mk(a.x * n, -a.y * n); }
 template <class T> __device__ __forceinline__ cx<T> dv(cx<T> a, cx<T> b) { return a * inv(b); }
 __device__ __forceinline__ float cabsf_(cf a) { return sqrtf(abs2(a)); }
+// The hardware approximations themselves (PTX rcp.approx / rsqrt.approx,
+// subnormals flushed): reciprocal within 1 ulp, reciprocal square root within
+// 2^-22.9 relative, one instruction each.  For the ray stage's normal-range
+// operands only.
+__device__ __forceinline__ float rcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_fast(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double cabs_(cd a) { return sqrt(abs2(a)); }
 __device__ __forceinline__ cf tof(cd a) { return mk((float)a.x, (float)a.y); }
 __device__ __forceinline__ cd tod(cf a) { return mk((double)a.x, (double)a.y); }

@@ -58,10 +58,9 @@ constexpr int MAXCELL = 96;      // (theta run, r run) cells
 constexpr int MAXBOX = 96;       // candidate sectors before merging
 constexpr int MAXANCH = 128;     // FP64 anchors per sector
 constexpr int GTH_MAX = 256;     // columns per theta group (at most)
-// Deferred boundary points per warp in the forward ray stage (8 words each):
-// 32, one per lane; 16 for a triple lens, whose 10 image slots per limb point
-// leave less shared memory for the FP64 point table.
-__host__ __device__ constexpr int dq_entries(int nl) { return nl == 2 ? 32 : 16; }
+// Deferred boundary points per warp in the forward ray stage: 32 (one per
+// lane when the queue is flushed), each a (column, row) pair.
+__host__ __device__ constexpr int dq_entries(int) { return 32; }
 constexpr int MAXCELL_D = 32;    // cells with tracked derivatives
 constexpr int MAXBOX_D = 32;     // candidate sectors with tracked derivatives
 constexpr float TINY_EXTENT = 3e-4f;  // images smaller than this x rho skip FP64 decisions
@@ -92,6 +91,24 @@ struct Anchor {
   float lo2;    // below: every ray of the group is inside the source (FP32 certain)
   float hi2;    // above: every ray of the group is outside (FP32 certain)
 };
+
+// The forward ray stage keeps, in the same table, U = sum_j K_j / Q_j (Q_j =
+// A_j + dz, dz the ray's offset from the anchor in the anchor's rotated
+// frame) as one quotient N / P of polynomials in dz, with N = sum_j K_j
+// prod_{k != j} Q_k and P = prod_j Q_j:
+//   binary:  N = n0 + n1 dz,             P = p0 + dz (p1 + dz)
+//   triple:  N = n0 + dz (n1 + dz n2),   P = p0 + dz (p1 + dz (p2 + dz))
+// (coefficients formed in FP64 and rounded once).
+struct AnchorF {
+  cf ws;        // as Anchor::ws
+  cf n[3];      // numerator coefficients
+  cf p[3];      // denominator coefficients (monic)
+  float e0;     // error bound constant part (as Anchor::e0)
+  float pad;
+  float lo2;    // as Anchor::lo2
+  float hi2;    // as Anchor::hi2
+};
+static_assert(sizeof(AnchorF) == sizeof(Anchor), "the two views share one table");
 
 using Box = BoxT<double>;
 
@@ -487,16 +504,17 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   double* pr = (double*)p;       p += sizeof(double) * PMAX;
   double* pt = (double*)p;       p += sizeof(double) * PMAX;
   int* queue = (int*)p;          p += sizeof(int) * QMAX;
+  p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);  // 16-byte rows of the offset table
   Anchor* anch = (Anchor*)p;     p += sizeof(Anchor) * MAXANCH;
-  cf* tab = (cf*)p;              p += sizeof(cf) * (GTH_MAX + 2);  // group offsets (two float arrays)
+  cf* tab = (cf*)p;              p += sizeof(cf) * (GTH_MAX + 2);  // group offsets (cos d - 1, sin d)
   const int seg = row_segment(g.n_theta, DER);  // rays per row segment
   float* rowbuf = (float*)p;     p += DER ? sizeof(float) * NW * (seg + 4) : 0;  // row buffers (derivative mode)
   cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
-  // boundary points: forward mode, a deferred queue per warp of 32 points x
-  // 8 words (stencil, row factor, indices); derivative mode, the indices of
-  // the current row segment's points
+  // boundary points: forward mode, a deferred queue per warp of (column,
+  // row) pairs; derivative mode, the indices of the current row segment's
+  // points
   (void)defer;
-  int* wqueue = (int*)p;         p += sizeof(int) * NW * (!DER ? 8 * dq_entries(NL) : 64);
+  int* wqueue = (int*)p;         p += sizeof(int) * NW * (!DER ? 2 * dq_entries(NL) : 64);
   // derivative mode: its state and the per-warp ray seeds
   DerShared& ds = *(DerShared*)p;  p += DER ? sizeof(DerShared) : 0;
   DualD* cdual = ds.cx;
@@ -1385,24 +1403,28 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         cd R = mk(cs, -sn);  // e^{-i th_c}
         cd zc = mk(rc * cs, rc * sn);
         cd wsd = lens_map<NL, double>(sh.L.eps, sh.L.a, zc) - sh.wc;
-        Anchor an_;
-        an_.ws = tof(R * wsd);
-        for (int j = 0; j < NL; ++j) {
-          cd Aj = R * (zc - sh.L.a[j]);
-          an_.A[j] = tof(Aj);
-          an_.K[j] = scl(inv(an_.A[j]), sh.eps32[j]);  // FP32 suffices (relative error of the U term)
-        }
+        const cf ws = tof(R * wsd);
         // error bound of |Delta w'|: anchor term plus rounding of the ray's
         // offset (at most the group half-diagonal) and of its image term
-        double half = 0.5 * gr * sh.dr64 + (B.r_hi) * 0.5 * gth * sh.dth64;
-        an_.e0 = (float)(16.0 * EPS32 * (fabs(an_.ws.x) + fabs(an_.ws.y) + 2.0 * half));
-        an_.e1 = (float)(16.0 * EPS32 * half);
-        // the same bound for the whole group: every ray has |dz| <= half, so
-        // |U|_1 <= sqrt(2) sum_j |K_j| / (|A_j| - half); squared distances
-        // outside [lo2, hi2] are decided in FP32 for every ray of the group
-        // (a superset of the per-ray uncertain band, with slack for the FP32
-        // evaluation of that band)
-        {
+        const double half = 0.5 * gr * sh.dr64 + (B.r_hi) * 0.5 * gth * sh.dth64;
+        const float e0 = (float)(16.0 * EPS32 * (fabs(ws.x) + fabs(ws.y) + 2.0 * half));
+        const double rr = (double)rho32 * (double)rho32;
+        float lo2 = -1.0f, hi2 = __int_as_float(0x7f800000);
+        if constexpr (DER) {
+          Anchor an_;
+          an_.ws = ws;
+          for (int j = 0; j < NL; ++j) {
+            cd Aj = R * (zc - sh.L.a[j]);
+            an_.A[j] = tof(Aj);
+            an_.K[j] = scl(inv(an_.A[j]), sh.eps32[j]);  // FP32 suffices (relative error of the U term)
+          }
+          an_.e0 = e0;
+          an_.e1 = (float)(16.0 * EPS32 * half);
+          // the same bound for the whole group: every ray has |dz| <= half, so
+          // |U|_1 <= sqrt(2) sum_j |K_j| / (|A_j| - half); squared distances
+          // outside [lo2, hi2] are decided in FP32 for every ray of the group
+          // (a superset of the per-ray uncertain band, with slack for the FP32
+          // evaluation of that band)
           double um = 0.0;
           bool bounded = true;
           for (int j = 0; j < NL; ++j) {
@@ -1410,32 +1432,85 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             if (!(aa > 1.0625 * half)) bounded = false;
             else um += sqrt((double)an_.K[j].x * an_.K[j].x + (double)an_.K[j].y * an_.K[j].y) / (aa - half);
           }
-          const double rr = (double)rho32 * (double)rho32;
           const double eb = (double)an_.e0 + (double)an_.e1 * 1.4142135623730951 * um;
           const double X = 1.01 * (2.0 * (double)rho32 * eb + eb * eb) + 8.0 * EPS32 * rr;
           if (bounded && X < 0.5 * rr) {
-            an_.lo2 = __double2float_rd(rr - X);
-            an_.hi2 = __double2float_ru(rr + X);
-          } else {
-            an_.lo2 = -1.0f;
-            an_.hi2 = __int_as_float(0x7f800000);
+            lo2 = __double2float_rd(rr - X);
+            hi2 = __double2float_ru(rr + X);
           }
+          an_.lo2 = lo2;
+          an_.hi2 = hi2;
+          anch[an] = an_;
+          ds.acs[an] = make_float2((float)cs, (float)sn);
+        } else {
+          // U = N / P (AnchorF), coefficients from the FP64 A_j, K_j
+          cd A64[NL], K64[NL];
+          for (int j = 0; j < NL; ++j) {
+            A64[j] = R * (zc - sh.L.a[j]);
+            K64[j] = scl(inv(A64[j]), sh.L.eps[j]);
+          }
+          cd nc[3], pc[3];
+          if constexpr (NL == 2) {
+            nc[0] = K64[0] * A64[1] + K64[1] * A64[0];
+            nc[1] = K64[0] + K64[1];
+            nc[2] = mk(0.0, 0.0);
+            pc[0] = A64[0] * A64[1];
+            pc[1] = A64[0] + A64[1];
+            pc[2] = mk(0.0, 0.0);
+          } else {
+            nc[0] = K64[0] * (A64[1] * A64[2]) + K64[1] * (A64[0] * A64[2]) + K64[2] * (A64[0] * A64[1]);
+            nc[1] = K64[0] * (A64[1] + A64[2]) + K64[1] * (A64[0] + A64[2]) + K64[2] * (A64[0] + A64[1]);
+            nc[2] = K64[0] + K64[1] + K64[2];
+            pc[0] = A64[0] * A64[1] * A64[2];
+            pc[1] = A64[0] * A64[1] + A64[0] * A64[2] + A64[1] * A64[2];
+            pc[2] = A64[0] + A64[1] + A64[2];
+          }
+          AnchorF af;
+          af.ws = ws;
+          for (int k = 0; k < 3; ++k) { af.n[k] = tof(nc[k]); af.p[k] = tof(pc[k]); }
+          af.e0 = e0;
+          af.pad = 0.f;
+          // the group's band: every ray has |dz| <= half, so |Q_j| >= |A_j| -
+          // half, |P| >= prod_j (|A_j| - half) and |U| <= sum_j |K_j| / (|A_j|
+          // - half); the rounding error of the FP32 quotient is bounded by
+          // u (cN M_N + (cP + 9) |U| M_P) / |P| (M_N, M_P: the polynomials
+          // with coefficient moduli, at |dz| = half) and that of dz U by
+          // |dz| (that + 3 u |U|), times 2 for the FP32 evaluation of the
+          // bound itself (see ray_eval)
+          bool bounded = true;
+          double um = 0.0, pmin = 1.0;
+          for (int j = 0; j < NL; ++j) {
+            const double aa = sqrt(abs2(A64[j]));
+            if (!(aa > 1.0625 * half)) bounded = false;
+            else { um += sqrt(abs2(K64[j])) / (aa - half); pmin *= aa - half; }
+          }
+          if (bounded) {
+            const double mn = sqrt(abs2(nc[0])) + half * (sqrt(abs2(nc[1])) + half * sqrt(abs2(nc[2])));
+            const double mp = NL == 2 ? sqrt(abs2(pc[0])) + half * (sqrt(abs2(pc[1])) + half)
+                                      : sqrt(abs2(pc[0])) + half * (sqrt(abs2(pc[1])) + half * (sqrt(abs2(pc[2])) + half));
+            const double cN = NL == 2 ? 4.0 : 9.0, cP = NL == 2 ? 6.0 : 13.0;
+            const double du = EPS32 * (cN * mn + (cP + 9.0) * um * mp) / pmin;
+            const double eb = (double)e0 + 2.0 * half * (du + 3.0 * EPS32 * um);
+            const double X = 1.01 * (2.0 * (double)rho32 * eb + eb * eb) + 8.0 * EPS32 * rr;
+            if (X < 0.5 * rr) {
+              lo2 = __double2float_rd(rr - X);
+              hi2 = __double2float_ru(rr + X);
+            }
+          }
+          af.lo2 = lo2;
+          af.hi2 = hi2;
+          reinterpret_cast<AnchorF*>(anch)[an] = af;
         }
-        anch[an] = an_;
-        if (DER) ds.acs[an] = make_float2((float)cs, (float)sn);
       }
-      // offsets within a theta group: (cos d - 1, sin d), d = (o + 1/2 - gth/2)
-      // dth, stored as two arrays (tabx, taby) so that a column pair's
-      // offsets load as one 8-byte word each
-      float* tabx = (float*)tab;
-      float* taby = tabx + gth;
+      // offsets within a theta group, (cos d - 1, sin d) with d = (o + 1/2 -
+      // gth/2) dth, one 8-byte pair per column (a column pair loads as 16
+      // bytes)
       for (int o = tid; o < gth; o += NT) {
         float d = ((float)o + 0.5f - 0.5f * (float)gth) * sh.dth32;
         float s, c;
         sincosf(d, &s, &c);
         float sh2 = sinf(0.5f * d);
-        tabx[o] = -2.0f * sh2 * sh2;
-        taby[o] = s;
+        tab[o] = mk(-2.0f * sh2 * sh2, s);
         (void)c;
       }
       __syncthreads();
@@ -1610,38 +1685,122 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       if constexpr (!DER) {
         // ---- forward ray stage.  A warp takes a task of 32 rows (lane = row
         // i) and a chunk [c0, c1) of theta columns, and sweeps the columns in
-        // order (all lanes at the same column, so the group offset table and,
-        // within an r group, the anchor are shared).  Each ray's squared
-        // distance is decided inside / outside in registers; the last five
-        // distances stay in a register ring, and a window of inside flags
-        // finds boundary points (inside with an outside neighbour), which go
-        // with their stencil to the per-warp deferred queue.  Every inside ray
-        // adds I(d) to its row; the queue adds I (W - 1) for the boundary
-        // points (Appendix A per-point rule).  One warp vote per column covers
-        // both rare events: a ray that FP32 cannot decide, and a boundary
-        // point to queue.
+        // blocks of KB (all lanes at the same column, so the group offsets
+        // and, within an r group, the anchor are shared and held in
+        // registers).  Each ray's squared distance is classified against the
+        // group's FP32 band: inside (I(d) added to the row), outside, or
+        // undecided.  The inside flags go into a per-lane bit window.  At the
+        // end of a block one warp vote covers both rare events: a ray the
+        // band left undecided (its own bound, else FP64, decides it) and a
+        // boundary point (inside with an outside neighbour), which goes to
+        // the per-warp deferred queue as (column, row).  A queue flush
+        // re-evaluates each point's five-ray stencil and adds I (W - 1)
+        // (Appendix A per-point rule).
         constexpr int DQ = dq_entries(NL);
-        float* dq = (float*)(wqueue + warp * 8 * DQ);
+        constexpr int KB = 8;  // columns per block (even: column pairs load as 16 bytes)
+        int2* dq = reinterpret_cast<int2*>(wqueue + warp * 2 * DQ);
         int dq_n = 0;
         const int CH = sh.chunk;
         const int nch = (NTH + CH - 1) / CH;
         const int ntask = ((NR + 31) >> 5) * nch;
         const float rr32 = rho32 * rho32;
         const unsigned lt_mask = (1u << lane) - 1u;
+        const AnchorF* anf = reinterpret_cast<const AnchorF*>(anch);
+        // c + a b in FP32, each operation rounded as written
+        auto cfma = [](const cf a, const cf b, const cf c) -> cf {
+          return mk(__fmaf_rn(a.x, b.x, __fmaf_rn(-a.y, b.y, c.x)), __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, c.y)));
+        };
+        // squared distance |Delta w'|^2 of the ray at group offset (tx, ty)
+        // in the row (ri_, dri_) of anchor an: Delta w' = ws + dz + conj(dz
+        // N / P), dz = (ri_ tx + dri_, ri_ ty).  Every operation is rounded
+        // as written, so each evaluation of a ray gives the same bits.  With
+        // eb: the ray's own bound on the error of |Delta w'|, e0 + 2 |dz| u
+        // (cN M_N + cU |U| M_P) / |P|, from |dN| <= cN u M_N, |dP| <= cP u
+        // M_P (Horner in complex FMAs, plus the rounded coefficients) and cU
+        // = 3 cP + 10 (the quotient, |P|^2, the reciprocal and the products),
+        // times 2 for the FP32 evaluation of the bound.
+        auto ray_eval = [&](const AnchorF& an, float tx, float ty, float ri_, float dri_, float* eb) -> float {
+          const cf dz = mk(__fmaf_rn(ri_, tx, dri_), __fmul_rn(ri_, ty));
+          cf Pq, Nq;
+          if constexpr (NL == 2) {
+            const cf F = mk(__fadd_rn(an.p[1].x, dz.x), __fadd_rn(an.p[1].y, dz.y));
+            Pq = cfma(dz, F, an.p[0]);
+            Nq = cfma(an.n[1], dz, an.n[0]);
+          } else {
+            const cf F2 = mk(__fadd_rn(an.p[2].x, dz.x), __fadd_rn(an.p[2].y, dz.y));
+            Pq = cfma(dz, cfma(dz, F2, an.p[1]), an.p[0]);
+            Nq = cfma(dz, cfma(an.n[2], dz, an.n[1]), an.n[0]);
+          }
+          const float q = __fmaf_rn(Pq.x, Pq.x, __fmul_rn(Pq.y, Pq.y));
+          const float ip = rcp_fast(q);  // <= 1 ulp
+          // V = N conj(P), pv = dz V, Delta w' = (ws + dz) + conj(pv) / |P|^2
+          const cf V = mk(__fmaf_rn(Nq.x, Pq.x, __fmul_rn(Nq.y, Pq.y)), __fmaf_rn(Nq.y, Pq.x, -__fmul_rn(Nq.x, Pq.y)));
+          const cf pv = mk(__fmaf_rn(dz.x, V.x, -__fmul_rn(dz.y, V.y)), __fmaf_rn(dz.x, V.y, __fmul_rn(dz.y, V.x)));
+          const cf dw = mk(__fmaf_rn(pv.x, ip, __fadd_rn(an.ws.x, dz.x)), __fmaf_rn(-pv.y, ip, __fadd_rn(an.ws.y, dz.y)));
+          if (eb) {
+            const float md = sqrtf(abs2(dz)), aP = sqrtf(q), aU = sqrtf(abs2(V)) * ip;
+            const float mn = sqrtf(abs2(an.n[0])) + md * (sqrtf(abs2(an.n[1])) + md * sqrtf(abs2(an.n[2])));
+            const float mp = NL == 2 ? sqrtf(abs2(an.p[0])) + md * (sqrtf(abs2(an.p[1])) + md)
+                                     : sqrtf(abs2(an.p[0])) + md * (sqrtf(abs2(an.p[1])) + md * (sqrtf(abs2(an.p[2])) + md));
+            constexpr float cN = NL == 2 ? 4.0f : 9.0f, cU = NL == 2 ? 28.0f : 49.0f;
+            *eb = an.e0 + 2.0f * md * EPS32 * (cN * mn + cU * aU * mp) / aP;
+          }
+          return __fmaf_rn(dw.x, dw.x, __fmul_rn(dw.y, dw.y));
+        };
+        // a ray the group band left open: its own bound decides in FP32 where
+        // it can, else the FP64 distance (d2 is then replaced by its square)
+        auto decide = [&](float& d2, float eb, int irow, int lw) -> bool {
+          const float X = 1.01f * (2.0f * rho32 * eb + eb * eb) + 8.0f * EPS32 * rr32;
+          if (fabsf(d2 - rr32) > X) return d2 < rr32;
+          const double d64 = ray_distance64<NL>(sh, B, irow, lw);
+          if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
+          d2 = (float)(d64 * d64);
+          return d64 < sh.rho;
+        };
+        // any column l of row irow (wrapped; beyond a non-periodic edge: outside, +inf)
+        auto classify = [&](int gi_, float ri_, float dri_, int irow, int l, float* d2o) -> bool {
+          if (!B.periodic && (l < 0 || l >= NTH)) { *d2o = __int_as_float(0x7f800000); return false; }
+          const int lw = wrapl(l);
+          const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
+          const AnchorF& an = anf[gi_ * mth + mgrp];
+          const cf t = tab[lw - mgrp * gth];
+          float eb;
+          float d2 = ray_eval(an, t.x, t.y, ri_, dri_, &eb);
+          bool in = d2 < an.lo2;
+          if (!in && !(d2 > an.hi2)) in = decide(d2, eb, irow, lw);
+          *d2o = d2;
+          return in;
+        };
+        // the queued points: one per lane, each re-evaluates its stencil
+        // (rays m - 2 .. m + 2, signed squared distances, negative inside)
         auto flush_queue = [&]() {
           __syncwarp();
           if (lane < dq_n) {
-            const float* e_ = dq + lane * 8;
-            const float I = brightness(-e_[2]);
-            float WU;
-            const float W = boundary_weight(0, e_, __float_as_int(e_[6]), __float_as_int(e_[7]), nullptr, &WU);
-            // literal rule: I (W - 1); split-profile rule: the limb value c0f
-            // with the uniform weight, the rest with f(delta)
-            const float term = split ? e_[5] * (c0f * (WU - 1.0f) + (I - c0f) * (W - 1.0f)) : e_[5] * I * (W - 1.0f);
-            const float y = term - acc_c;
-            const float tt = acc_s + y;
-            acc_c = (tt - acc_s) - y;
-            acc_s = tt;
+            const int2 q_ = dq[lane];
+            const int m = q_.x, irow = q_.y;
+            const int gi_ = irow / gr;
+            const float dri_ = ((float)(irow - gi_ * gr) + 0.5f - 0.5f * (float)gr) * dr32;
+            const float ri_ = (float)(B.r_lo + (gi_ * gr + 0.5 * gr) * sh.dr64) + dri_;
+            float sv[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+              float d2;
+              const bool in = classify(gi_, ri_, dri_, irow, m - 2 + k, &d2);
+              sv[k] = in ? __int_as_float(__float_as_int(d2) | 0x80000000) : d2;
+            }
+            if (signbit(sv[2])) {
+              const float I = brightness(-sv[2]);
+              float WU;
+              const float W = boundary_weight(0, sv, m, irow, nullptr, &WU);
+              const float rw = ri_ * bxw;
+              // literal rule: I (W - 1); split-profile rule: the limb value c0f
+              // with the uniform weight, the rest with f(delta)
+              const float term = split ? rw * (c0f * (WU - 1.0f) + (I - c0f) * (W - 1.0f)) : rw * I * (W - 1.0f);
+              const float y = term - acc_c;
+              const float tt = acc_s + y;
+              acc_c = (tt - acc_s) - y;
+              acc_s = tt;
+            }
           }
           __syncwarp();
           dq_n = 0;
@@ -1659,180 +1818,112 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           const float dri = ((float)(ii - gi * gr) + 0.5f - 0.5f * (float)gr) * dr32;
           const float ri = (float)(B.r_lo + (gi * gr + 0.5 * gr) * sh.dr64) + dri;
           const int c0 = chk * CH, c1 = min(c0 + CH, NTH);
-          // anchor of the current theta group (registers)
-          int a_grp = -1, a_next = 0, a_idx = 0;
-          cf a_ws, a_A[NL], a_K[NL];
-          float a_lo2 = 0.f, a_hi2 = 0.f;
-          const float* tpx = tabx;
-          const float* tpy = taby;
-          auto load_group = [&](int lw) {
-            const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
-            if (mgrp == a_grp) return;
-            a_grp = mgrp;
-            a_next = (mgrp + 1) * gth;
-            a_idx = gi * mth + mgrp;
-            const Anchor& an_ = anch[a_idx];
-            a_ws = an_.ws;
-#pragma unroll
-            for (int j = 0; j < NL; ++j) { a_A[j] = an_.A[j]; a_K[j] = an_.K[j]; }
-            a_lo2 = an_.lo2;
-            a_hi2 = an_.hi2;
-            tpx = tabx - mgrp * gth;
-            tpy = taby - mgrp * gth;
-          };
-          unsigned win = 0u;  // inside flags: bit k = column l - k
           float rowacc = 0.f;
-          // squared distance of ray (i, lw) in FP32 (difference form about the
-          // group's anchor) and |U|_1 for its own error bound
-          auto ray = [&](int lw, float* uab) -> float {
-            const cf t = mk(tpx[lw], tpy[lw]);
-            const cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
-            cf U;
-            if constexpr (NL == 2) {
-              const cf Q0 = a_A[0] + dz, Q1 = a_A[1] + dz;
-              const float n0 = abs2(Q0), n1 = abs2(Q1);
-              const float ip = __fdividef(1.0f, n0 * n1);  // <= 2 ulp, inside the error bound
-              const cf t0 = a_K[0] * cj(Q0), t1 = a_K[1] * cj(Q1);
-              U = scl(scl(t0, n1) + scl(t1, n0), ip);
-            } else {
-              const cf Q0 = a_A[0] + dz, Q1 = a_A[1] + dz, Q2 = a_A[2] + dz;
-              const float n0 = abs2(Q0), n1 = abs2(Q1), n2 = abs2(Q2);
-              const float n01 = n0 * n1;
-              const float ip = __fdividef(1.0f, n01 * n2);
-              const cf t0 = a_K[0] * cj(Q0), t1 = a_K[1] * cj(Q1), t2 = a_K[2] * cj(Q2);
-              U = scl(scl(t0, n1 * n2) + scl(t1, n0 * n2) + scl(t2, n01), ip);
+          float dh;
+          // inside flags: bit k = column l - 1 - k before column l; the left
+          // halo column c0 - 1 first
+          unsigned win = classify(gi, ri, dri, ii, c0 - 1, &dh) ? 1u : 0u;
+          AnchorF ar;           // the current group's anchor
+          const cf* tp = tab;   // offsets of the current group, by column
+          // queue the boundary points among bits of bm, bit j = column base - j
+          auto push_bits = [&](unsigned bm, int base) {
+            while (__any_sync(0xffffffffu, bm != 0u)) {
+              const bool has = bm != 0u;
+              const int m = base - (has ? __ffs(bm) - 1 : 0);
+              bm &= bm - 1u;
+              unsigned rem = __ballot_sync(0xffffffffu, has);
+              // up to 32 points, the queue holds DQ: take the lowest set
+              // lanes that fit, flushing whenever the queue is full
+              while (rem) {
+                if (dq_n == DQ) flush_queue();
+                unsigned take = rem;
+                const int room = DQ - dq_n;
+                if (__popc(take) > room) {
+                  take = 0u;
+                  unsigned r = rem;
+                  for (int k = 0; k < room; ++k) {
+                    const unsigned low = r & (0u - r);
+                    take |= low;
+                    r ^= low;
+                  }
+                }
+                if (take & (1u << lane)) dq[dq_n + __popc(take & lt_mask)] = make_int2(m, i);
+                dq_n += __popc(take);
+                rem &= ~take;
+              }
             }
-            const cf pz = dz * U;
-            const cf dw = mk(a_ws.x + dz.x + pz.x, a_ws.y + dz.y - pz.y);
-            *uab = fabsf(U.x) + fabsf(U.y);
-            return abs2(dw);
           };
-          // the ray's own bound decides; FP64 where it cannot
-          auto resolve = [&](float& d2, float uab, int lw) -> bool {
-            const Anchor& an_ = anch[a_idx];
-            const float eb = fmaf(an_.e1, uab, an_.e0);
-            if (fabsf(d2 - rr32) <= 2.0f * rho32 * eb + eb * eb) {
-              const double d64 = ray_distance64<NL>(sh, B, ii, lw);
-              if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
-              d2 = (float)(d64 * d64);
-              return d64 < sh.rho;
+          // boundary centres among columns l0 - 1 .. l0 + nb - 2 (bit j =
+          // column l0 + nb - 2 - j) after the block [l0, l0 + nb); the first
+          // block's column c0 - 1 belongs to the previous chunk
+          auto centres = [&](int nb, bool first) -> unsigned {
+            unsigned bm = ((win & ~((win << 1) & (win >> 1))) >> 1) & ((1u << nb) - 1u);
+            if (first) bm &= ~(1u << (nb - 1));
+            return rowok ? bm : 0u;
+          };
+          auto block_end = [&](int l0, int nb, bool first, bool unc) {
+            unsigned bm = centres(nb, first);
+            if (__any_sync(0xffffffffu, unc || bm != 0u)) {
+              if (unc) {
+                for (int k = 0; k < nb; ++k) {
+                  const cf t = tp[l0 + k];
+                  float eb;
+                  float d2 = ray_eval(ar, t.x, t.y, ri, dri, &eb);
+                  if (d2 < ar.lo2 || d2 > ar.hi2) continue;
+                  if (decide(d2, eb, ii, l0 + k)) {
+                    win |= 1u << (nb - 1 - k);
+                    rowacc += brightness(d2);
+                  }
+                }
+                bm = centres(nb, first);
+              }
+              push_bits(bm, l0 + nb - 2);
             }
-            return d2 < rr32;
           };
-          // queue boundary point m = l - 2 with its stencil (v[m-2..m+2]) =
-          // (a, b, c, d, e), the inside flags at bits 4..0 of win
-          auto push = [&](bool isb, int m, float a, float b, float c, float d, float e) {
-            unsigned rem = __ballot_sync(0xffffffffu, isb);
-            // up to 32 points, the queue holds DQ: take the lowest set lanes
-            // that fit, flushing whenever the queue is full (warp-uniform)
-            while (rem) {
-              if (dq_n == DQ) flush_queue();
-              unsigned take = rem;
-              const int room = DQ - dq_n;
-              if (__popc(take) > room) {
-                take = 0u;
-                unsigned r = rem;
-                for (int k = 0; k < room; ++k) {
-                  const unsigned low = r & (0u - r);
-                  take |= low;
-                  r ^= low;
+          // one column: classify against the band, flag, add I(d) if inside
+          // (x > 5 u there, as d^2 < lo2 <= rho^2 (1 - 8 u))
+          auto col = [&](float tx, float ty, bool& unc) {
+            const float d2 = ray_eval(ar, tx, ty, ri, dri, nullptr);
+            const bool in = d2 < ar.lo2;
+            unc = unc || !(in || d2 > ar.hi2);
+            win = (win << 1) | (in ? 1u : 0u);
+            const float x = __fmaf_rn(-d2, irho2, 1.0f);
+            const float I = fmaf(c2f, x, fmaf(c1f, x * rsqrt_fast(x), c0f));
+            rowacc += in ? I : 0.0f;
+          };
+          int l = c0;
+          bool first = true;
+          while (l < c1) {
+            const int mgrp = (int)__umulhi((unsigned int)l, gmagic);
+            ar = anf[gi * mth + mgrp];
+            tp = tab - mgrp * gth;
+            const int lend = min((mgrp + 1) * gth, c1);
+            while (l < lend) {
+              const int nb = min(KB, lend - l);
+              bool unc = false;
+              if (nb == KB) {
+#pragma unroll
+                for (int k = 0; k < KB; k += 2) {
+                  // columns l + k, l + k + 1 (l + k even: a 16-byte row)
+                  const float4 t2 = *reinterpret_cast<const float4*>(tp + l + k);
+                  col(t2.x, t2.y, unc);
+                  col(t2.z, t2.w, unc);
+                }
+              } else {
+#pragma unroll 1
+                for (int k = 0; k < nb; ++k) {
+                  const cf t = tp[l + k];
+                  col(t.x, t.y, unc);
                 }
               }
-              if (take & (1u << lane)) {
-                float* e_ = dq + (dq_n + __popc(take & lt_mask)) * 8;
-                const float v5[5] = {a, b, c, d, e};
-#pragma unroll
-                for (int k = 0; k < 5; ++k)
-                  e_[k] = __int_as_float(__float_as_int(v5[k]) | (((win >> (4 - k)) & 1u) << 31));
-                e_[5] = ri * bxw;
-                e_[6] = __int_as_float(m);
-                e_[7] = __int_as_float(i);
-              }
-              dq_n += __popc(take);
-              rem &= ~take;
-            }
-          };
-          // main column l (inside [c0, c1), no wrap; the group already
-          // loaded): ring (a, b, c, d) = v[l-4..l-1], result into dst.  The
-          // boundary test of the centre m = l - 2 needs only the flags of
-          // l - 3 .. l - 1 (bits 0..2 of win before the shift), so it shares
-          // the column's vote.
-          auto main_col = [&](int l, bool fin, float& dst, float a, float b, float c, float d) {
-            float uab;
-            float d2 = ray(l, &uab);
-            bool in = d2 < a_lo2;
-            const bool unc = !in && !(d2 > a_hi2);
-            const bool isb = fin && rowok && (win & 2u) && ((win & 5u) != 5u);
-            if (__any_sync(0xffffffffu, unc || isb)) {
-              if (unc) in = resolve(d2, uab, l);
-              win = (win << 1) | (in ? 1u : 0u);
-              push(isb, l - 2, a, b, c, d, d2);
-            } else {
-              win = (win << 1) | (in ? 1u : 0u);
-            }
-            if (in) rowacc += brightness(d2);
-            dst = d2;
-          };
-          // halo column (wrapped, or beyond a non-periodic edge)
-          auto halo = [&](int l) -> float {
-            const bool beyond = !B.periodic && (l < 0 || l >= NTH);
-            float d2 = __int_as_float(0x7f800000);
-            bool in = false;
-            if (!beyond) {
-              const int lw = wrapl(l);
-              load_group(lw);
-              float uab;
-              d2 = ray(lw, &uab);
-              in = d2 < a_lo2;
-              const bool unc = !in && !(d2 > a_hi2);
-              if (__any_sync(0xffffffffu, unc))
-                if (unc) in = resolve(d2, uab, lw);
-            }
-            win = (win << 1) | (in ? 1u : 0u);
-            return d2;
-          };
-          float r0 = 0.f, r1 = 0.f, r2 = 0.f, r3, r4;
-          r3 = halo(c0 - 2);
-          r4 = halo(c0 - 1);
-          // main columns: ring r0..r4 holds v[l-5..l-1] before column l; the
-          // first two finalize nothing (their centres are halo columns)
-          int l = c0;
-          load_group(l);
-#pragma unroll 1
-          for (int k = 0; k < 2 && l < c1; ++k, ++l) {
-            if (l >= a_next) load_group(l);
-            float nv;
-            main_col(l, false, nv, r1, r2, r3, r4);
-            r0 = r1; r1 = r2; r2 = r3; r3 = r4; r4 = nv;
-          }
-#pragma unroll 1
-          while (l < c1) {
-            if (l >= a_next) load_group(l);
-            // columns up to the group end or the chunk end, five at a time
-            const int lend = min(a_next, c1);
-#pragma unroll 1
-            for (; l + 5 <= lend; l += 5) {
-              main_col(l + 0, true, r0, r1, r2, r3, r4);
-              main_col(l + 1, true, r1, r2, r3, r4, r0);
-              main_col(l + 2, true, r2, r3, r4, r0, r1);
-              main_col(l + 3, true, r3, r4, r0, r1, r2);
-              main_col(l + 4, true, r4, r0, r1, r2, r3);
-            }
-#pragma unroll 1
-            for (; l < lend; ++l) {
-              float nv;
-              main_col(l, true, nv, r1, r2, r3, r4);
-              r0 = r1; r1 = r2; r2 = r3; r3 = r4; r4 = nv;
+              block_end(l, nb, first, unc);
+              first = false;
+              l += nb;
             }
           }
-          // right halo: finalizes the last two columns of the chunk
-#pragma unroll 1
-          for (int k = 0; k < 2; ++k, ++l) {
-            const bool isb = l - 2 >= c0 && rowok && (win & 2u) && ((win & 5u) != 5u);
-            const float nv = halo(l);
-            if (__any_sync(0xffffffffu, isb)) push(isb, l - 2, r1, r2, r3, r4, nv);
-            r0 = r1; r1 = r2; r2 = r3; r3 = r4; r4 = nv;
-          }
+          // right halo column c1: finalizes column c1 - 1
+          win = (win << 1) | (classify(gi, ri, dri, ii, c1, &dh) ? 1u : 0u);
+          push_bits(rowok ? (((win & ~((win << 1) & (win >> 1))) >> 1) & 1u) : 0u, c1 - 1);
           if (rowok) {
             const float term = ri * rowacc * bxw;
             const float y = term - acc_c;
@@ -1865,7 +1956,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
             const int o = lw - mgrp * gth;
             const Anchor& an_ = anch[gi * mth + mgrp];
-            cf t = mk(tabx[o], taby[o]);
+            cf t = tab[o];
             cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
             cf U;
             if constexpr (NL == 2) {
@@ -2043,7 +2134,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
               const int o = lw - mgrp * gth;
               const Anchor& an_ = anch[gi * mth + mgrp];
-              const cf t = mk(tabx[o], taby[o]);
+              const cf t = tab[o];
               const cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
               const cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz;
               const float n0 = abs2(Q0), n1 = abs2(Q1);
@@ -2275,10 +2366,10 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += sizeof(cf) * NP + 4 * sizeof(float) * NP;
   b += sizeof(short) * ((NP + 7) & ~(size_t)7);
   b += 3 * ((NP + 15) & ~(size_t)15);
-  b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + sizeof(Anchor) * MAXANCH;
+  b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + 16 + sizeof(Anchor) * MAXANCH;
   const int NW = nt / 32;
   (void)defer;
-  b += sizeof(int) * NW * (!der ? 8 * dq_entries(NL) : 64);  // per-warp boundary queues
+  b += sizeof(int) * NW * (!der ? 2 * dq_entries(NL) : 64);  // per-warp boundary queues
   const int seg = row_segment(g.n_theta, der);
   if (der) b += sizeof(DerShared) + 2 * sizeof(float) * NW * (seg + 4);  // state, row buffers and ray seeds
   b += sizeof(cf) * (GTH_MAX + 2);
