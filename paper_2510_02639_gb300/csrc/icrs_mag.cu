@@ -37,16 +37,15 @@
 
 namespace icrs {
 
-// Threads per block (one block per SM).  The binary forward kernel runs 640
-// threads (96 registers): its ray stage keeps a whole column step in
-// registers and is bound by instruction issue and dependency latency, so it
-// gains from more warps (at 1024 x 2048: 512 threads 13.7 ms, 576 12.8 ms,
-// 640 11.8 ms on a 320-epoch sample), but at 704 threads (88 registers) it
-// spills and takes 21 ms.  Where the wider layout does not fit in shared
-// memory it falls back to a 512-thread instantiation.  The derivative and
-// triple instantiations keep 512 threads (128 registers): with fewer their
-// FP64 phases spill kilobytes.
-constexpr int NT_WIDE = 640, NT_BASE = 512;
+// Threads per block (one block per SM).  The binary forward kernel's ray
+// stage evaluates two columns per paired FP32 instruction and is bound by
+// dependency latency more than by issue: registers for independent column
+// pairs pay more than further warps (at 1024 x 2048 on a 320-epoch sample:
+// 512 threads 6.66 ms, 576 6.86, 640 6.93, 768 7.01).  NT_WIDE is the binary
+// forward block size (with a 512-thread fallback where its layout does not
+// fit in shared memory); the derivative and triple instantiations keep 512
+// threads (128 registers): with fewer their FP64 phases spill kilobytes.
+constexpr int NT_WIDE = 512, NT_BASE = 512;
 __host__ __device__ constexpr int mag_threads(int nl, bool der) { return (nl == 2 && !der) ? NT_WIDE : NT_BASE; }
 constexpr int NW_MAX = NT_WIDE / 32;  // warps per block, largest instantiation
 constexpr int NW_DER = NT_BASE / 32;  // warps per block, derivative mode
@@ -1503,17 +1502,24 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         }
       }
       // offsets within a theta group, (cos d - 1, sin d) with d = (o + 1/2 -
-      // gth/2) dth, one 8-byte pair per column (a column pair loads as 16
-      // bytes)
+      // gth/2) dth; column pairs (o, o + 1), o even, are stored as 16 bytes
+      // (x_o, x_o+1, y_o, y_o+1), so that the forward ray stage loads a pair's
+      // x and y as two adjacent float2 (gth is even)
+      float* tabf = reinterpret_cast<float*>(tab);
       for (int o = tid; o < gth; o += NT) {
         float d = ((float)o + 0.5f - 0.5f * (float)gth) * sh.dth32;
         float s, c;
         sincosf(d, &s, &c);
         float sh2 = sinf(0.5f * d);
-        tab[o] = mk(-2.0f * sh2 * sh2, s);
+        tabf[4 * (o >> 1) + (o & 1)] = -2.0f * sh2 * sh2;
+        tabf[4 * (o >> 1) + 2 + (o & 1)] = s;
         (void)c;
       }
       __syncthreads();
+      auto tab_at = [&](int o) -> cf {
+        const float* t_ = tabf + 4 * (o >> 1) + (o & 1);
+        return mk(t_[0], t_[2]);
+      };
       const float dr32 = sh.dr32;
       const float bxw = (float)(sh.dr64 * sh.dth64);
       auto wrapl = [&](int l) -> int { return l < 0 ? l + NTH : (l >= NTH ? l - NTH : l); };
@@ -1747,6 +1753,43 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           }
           return __fmaf_rn(dw.x, dw.x, __fmul_rn(dw.y, dw.y));
         };
+        // the anchor as broadcast pairs for two columns at once (binary)
+        struct AnchorP { float2 wsx, wsy, n0x, n0y, n1x, n1y, nn1y, p0x, p0y, p1x, p1y; };
+        auto pairs_of = [](const AnchorF& a) -> AnchorP {
+          AnchorP r;
+          r.wsx = make_float2(a.ws.x, a.ws.x);     r.wsy = make_float2(a.ws.y, a.ws.y);
+          r.n0x = make_float2(a.n[0].x, a.n[0].x); r.n0y = make_float2(a.n[0].y, a.n[0].y);
+          r.n1x = make_float2(a.n[1].x, a.n[1].x); r.n1y = make_float2(a.n[1].y, a.n[1].y);
+          r.nn1y = make_float2(-a.n[1].y, -a.n[1].y);
+          r.p0x = make_float2(a.p[0].x, a.p[0].x); r.p0y = make_float2(a.p[0].y, a.p[0].y);
+          r.p1x = make_float2(a.p[1].x, a.p[1].x); r.p1y = make_float2(a.p[1].y, a.p[1].y);
+          return r;
+        };
+        // rays of columns (l, l + 1) of one row with paired FP32 operations
+        // (binary lens): component k is rounded exactly as ray_eval rounds
+        // ray l + k, operation by operation, so both give the same bits
+        auto ray_eval2 = [&](const AnchorP& a, float2 tx, float2 ty, float2 ri2, float2 dri2) -> float2 {
+          const float2 dzx = __ffma2_rn(ri2, tx, dri2), dzy = __fmul2_rn(ri2, ty);
+          const float2 ndzy = make_float2(-dzy.x, -dzy.y);
+          const float2 Fx = __fadd2_rn(a.p1x, dzx), Fy = __fadd2_rn(a.p1y, dzy);
+          const float2 Px = __ffma2_rn(dzx, Fx, __ffma2_rn(ndzy, Fy, a.p0x));
+          const float2 Py = __ffma2_rn(dzx, Fy, __ffma2_rn(dzy, Fx, a.p0y));
+          const float2 Nx = __ffma2_rn(a.n1x, dzx, __ffma2_rn(a.nn1y, dzy, a.n0x));
+          const float2 Ny = __ffma2_rn(a.n1x, dzy, __ffma2_rn(a.n1y, dzx, a.n0y));
+          const float2 q = __ffma2_rn(Px, Px, __fmul2_rn(Py, Py));
+          const float2 ip = make_float2(rcp_fast(q.x), rcp_fast(q.y));
+          const float2 m1 = __fmul2_rn(Nx, Py);
+          const float2 Vx = __ffma2_rn(Nx, Px, __fmul2_rn(Ny, Py));
+          const float2 Vy = __ffma2_rn(Ny, Px, make_float2(-m1.x, -m1.y));
+          const float2 m2 = __fmul2_rn(dzy, Vy);
+          const float2 pvx = __ffma2_rn(dzx, Vx, make_float2(-m2.x, -m2.y));
+          const float2 pvy = __ffma2_rn(dzx, Vy, __fmul2_rn(dzy, Vx));
+          const float2 dwx = __ffma2_rn(pvx, ip, __fadd2_rn(a.wsx, dzx));
+          const float2 dwy = __ffma2_rn(make_float2(-pvy.x, -pvy.y), ip, __fadd2_rn(a.wsy, dzy));
+          return __ffma2_rn(dwx, dwx, __fmul2_rn(dwy, dwy));
+        };
+        const float2 irho22 = make_float2(irho2, irho2), one2 = make_float2(1.0f, 1.0f);
+        const float2 c1f2 = make_float2(c1f, c1f), c2f2 = make_float2(c2f, c2f);
         // a ray the group band left open: its own bound decides in FP32 where
         // it can, else the FP64 distance (d2 is then replaced by its square)
         auto decide = [&](float& d2, float eb, int irow, int lw) -> bool {
@@ -1763,7 +1806,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           const int lw = wrapl(l);
           const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
           const AnchorF& an = anf[gi_ * mth + mgrp];
-          const cf t = tab[lw - mgrp * gth];
+          const cf t = tab_at(lw - mgrp * gth);
           float eb;
           float d2 = ray_eval(an, t.x, t.y, ri_, dri_, &eb);
           bool in = d2 < an.lo2;
@@ -1818,13 +1861,27 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           const float dri = ((float)(ii - gi * gr) + 0.5f - 0.5f * (float)gr) * dr32;
           const float ri = (float)(B.r_lo + (gi * gr + 0.5 * gr) * sh.dr64) + dri;
           const int c0 = chk * CH, c1 = min(c0 + CH, NTH);
-          float rowacc = 0.f;
+          // the row's inside rays: their count, and the sums of I - c0f =
+          // mu (c1f + c2f mu) of the scalar and of the paired evaluations
+          int cnt = 0;
+          float sj = 0.f;
+          float2 sj2 = make_float2(0.f, 0.f);
           float dh;
           // inside flags: bit k = column l - 1 - k before column l; the left
           // halo column c0 - 1 first
           unsigned win = classify(gi, ri, dri, ii, c0 - 1, &dh) ? 1u : 0u;
-          AnchorF ar;           // the current group's anchor
-          const cf* tp = tab;   // offsets of the current group, by column
+          float lo2g = 0.f, hi2g = 0.f;  // the current group's band
+          int aidx = 0;                  // and its anchor
+          AnchorF ar;     // the anchor in registers (triple)
+          AnchorP ap;     // the anchor as broadcast pairs (binary)
+          // binary: the scalar evaluations read the anchor from the table
+          auto anchor = [&]() -> const AnchorF& {
+            if constexpr (NL == 2) return anf[aidx];
+            else return ar;
+          };
+          int gbase = 0;  // first column of the current group
+          const float* tpf = tabf;  // offsets of the current group: pair rows by column
+          const float2 ri2 = make_float2(ri, ri), dri2 = make_float2(dri, dri);
           // queue the boundary points among bits of bm, bit j = column base - j
           auto push_bits = [&](unsigned bm, int base) {
             while (__any_sync(0xffffffffu, bm != 0u)) {
@@ -1861,58 +1918,81 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             if (first) bm &= ~(1u << (nb - 1));
             return rowok ? bm : 0u;
           };
+          // an inside ray's share of the row beyond c0f: mu (c1f + c2f mu)
+          auto add_in = [&](bool in, float mu) { sj = __fadd_rn(sj, in ? mu * fmaf(c2f, mu, c1f) : 0.0f); };
           auto block_end = [&](int l0, int nb, bool first, bool unc) {
             unsigned bm = centres(nb, first);
             if (__any_sync(0xffffffffu, unc || bm != 0u)) {
               if (unc) {
                 for (int k = 0; k < nb; ++k) {
-                  const cf t = tp[l0 + k];
+                  const cf t = tab_at(l0 + k - gbase);
                   float eb;
-                  float d2 = ray_eval(ar, t.x, t.y, ri, dri, &eb);
-                  if (d2 < ar.lo2 || d2 > ar.hi2) continue;
+                  float d2 = ray_eval(anchor(), t.x, t.y, ri, dri, &eb);
+                  if (d2 < lo2g || d2 > hi2g) continue;
                   if (decide(d2, eb, ii, l0 + k)) {
                     win |= 1u << (nb - 1 - k);
-                    rowacc += brightness(d2);
+                    add_in(true, sqrtf(fmaxf(__fmaf_rn(-d2, irho2, 1.0f), 0.0f)));
                   }
                 }
                 bm = centres(nb, first);
               }
               push_bits(bm, l0 + nb - 2);
             }
+            cnt += __popc(win & ((1u << nb) - 1u));
           };
-          // one column: classify against the band, flag, add I(d) if inside
-          // (x > 5 u there, as d^2 < lo2 <= rho^2 (1 - 8 u))
+          // one column: classify against the band, flag, and if inside add
+          // its mu (x > 5 u there, as d^2 < lo2 <= rho^2 (1 - 8 u))
           auto col = [&](float tx, float ty, bool& unc) {
-            const float d2 = ray_eval(ar, tx, ty, ri, dri, nullptr);
-            const bool in = d2 < ar.lo2;
-            unc = unc || !(in || d2 > ar.hi2);
+            const float d2 = ray_eval(anchor(), tx, ty, ri, dri, nullptr);
+            const bool in = d2 < lo2g;
+            unc = unc || !(in || d2 > hi2g);
             win = (win << 1) | (in ? 1u : 0u);
             const float x = __fmaf_rn(-d2, irho2, 1.0f);
-            const float I = fmaf(c2f, x, fmaf(c1f, x * rsqrt_fast(x), c0f));
-            rowacc += in ? I : 0.0f;
+            add_in(in, __fmul_rn(x, rsqrt_fast(x)));
+          };
+          // two columns (l, l + 1) with paired operations (binary lens); the
+          // pair row t4 = (x_l, x_l+1, y_l, y_l+1)
+          auto col2 = [&](const float4 t4, bool& unc) {
+            const float2 d2 = ray_eval2(ap, make_float2(t4.x, t4.y), make_float2(t4.z, t4.w), ri2, dri2);
+            const bool in0 = d2.x < lo2g, in1 = d2.y < lo2g;
+            unc = unc || !(in0 || d2.x > hi2g) || !(in1 || d2.y > hi2g);
+            win = (win << 2) | (in0 ? 2u : 0u) | (in1 ? 1u : 0u);
+            const float2 x = __ffma2_rn(make_float2(-d2.x, -d2.y), irho22, one2);
+            const float2 mu = __fmul2_rn(x, make_float2(rsqrt_fast(x.x), rsqrt_fast(x.y)));
+            const float2 J = __fmul2_rn(mu, __ffma2_rn(c2f2, mu, c1f2));
+            sj2 = __fadd2_rn(sj2, make_float2(in0 ? J.x : 0.0f, in1 ? J.y : 0.0f));
           };
           int l = c0;
           bool first = true;
           while (l < c1) {
             const int mgrp = (int)__umulhi((unsigned int)l, gmagic);
-            ar = anf[gi * mth + mgrp];
-            tp = tab - mgrp * gth;
-            const int lend = min((mgrp + 1) * gth, c1);
+            aidx = gi * mth + mgrp;
+            lo2g = anf[aidx].lo2;
+            hi2g = anf[aidx].hi2;
+            if constexpr (NL == 2) ap = pairs_of(anf[aidx]);
+            else ar = anf[aidx];
+            gbase = mgrp * gth;
+            tpf = tabf - 2 * gbase;
+            const int lend = min(gbase + gth, c1);
             while (l < lend) {
               const int nb = min(KB, lend - l);
               bool unc = false;
               if (nb == KB) {
 #pragma unroll
                 for (int k = 0; k < KB; k += 2) {
-                  // columns l + k, l + k + 1 (l + k even: a 16-byte row)
-                  const float4 t2 = *reinterpret_cast<const float4*>(tp + l + k);
-                  col(t2.x, t2.y, unc);
-                  col(t2.z, t2.w, unc);
+                  // columns l + k, l + k + 1 (l + k - gbase even: one 16-byte row)
+                  const float4 t4 = *reinterpret_cast<const float4*>(tpf + 2 * (l + k));
+                  if constexpr (NL == 2) {
+                    col2(t4, unc);
+                  } else {
+                    col(t4.x, t4.z, unc);
+                    col(t4.y, t4.w, unc);
+                  }
                 }
               } else {
 #pragma unroll 1
                 for (int k = 0; k < nb; ++k) {
-                  const cf t = tp[l + k];
+                  const cf t = tab_at(l + k - gbase);
                   col(t.x, t.y, unc);
                 }
               }
@@ -1925,6 +2005,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           win = (win << 1) | (classify(gi, ri, dri, ii, c1, &dh) ? 1u : 0u);
           push_bits(rowok ? (((win & ~((win << 1) & (win >> 1))) >> 1) & 1u) : 0u, c1 - 1);
           if (rowok) {
+            const float rowacc = c0f * (float)cnt + (sj + (sj2.x + sj2.y));
             const float term = ri * rowacc * bxw;
             const float y = term - acc_c;
             const float tt = acc_s + y;
@@ -1956,7 +2037,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
             const int o = lw - mgrp * gth;
             const Anchor& an_ = anch[gi * mth + mgrp];
-            cf t = tab[o];
+            cf t = tab_at(o);
             cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
             cf U;
             if constexpr (NL == 2) {
@@ -2134,7 +2215,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
               const int o = lw - mgrp * gth;
               const Anchor& an_ = anch[gi * mth + mgrp];
-              const cf t = tab[o];
+              const cf t = tab_at(o);
               const cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
               const cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz;
               const float n0 = abs2(Q0), n1 = abs2(Q1);
