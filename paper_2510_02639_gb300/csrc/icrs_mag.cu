@@ -70,44 +70,26 @@ constexpr float EPS32 = 5.9604645e-8f;  // 2^-24
 constexpr float EE_SUSPECT = 1e-6f;
 constexpr float DUP_TOL = 1e-6f;
 
-// Rays per row segment of the derivative mode's row buffers: 256 (its per-ray
-// seeds take the same room again).  (The forward ray stage keeps no row
-// buffer.)
-__host__ __device__ __forceinline__ int row_segment(int n_theta, bool der) {
-  const int segmax = der ? 256 : 508;
-  return n_theta < segmax ? n_theta : segmax;
-}
-
 // Meta bits of an image-limb slot.
 constexpr uint8_t M_VALID = 1, M_EXACT = 2, M_UNSURE = 4, M_CAND = 8;
 
-struct Anchor {
-  cf ws;        // e^{-i th_m} (f(z_m) - w_c)
-  cf A[3];      // e^{-i th_m} (z_m - a_j)
-  cf K[3];      // eps_j / A_j
-  float e0;     // error bound constant part
-  float e1;     // error bound factor of |U|_1
-  float lo2;    // below: every ray of the group is inside the source (FP32 certain)
-  float hi2;    // above: every ray of the group is outside (FP32 certain)
-};
-
-// The forward ray stage keeps, in the same table, U = sum_j K_j / Q_j (Q_j =
-// A_j + dz, dz the ray's offset from the anchor in the anchor's rotated
-// frame) as one quotient N / P of polynomials in dz, with N = sum_j K_j
-// prod_{k != j} Q_k and P = prod_j Q_j:
+// Anchor of a (theta group, r group) of a sector: the rays' squared distance
+// is evaluated about it in FP32 with U = sum_j K_j / Q_j (A_j = e^{-i th_m}
+// (z_m - a_j), K_j = eps_j / A_j, Q_j = A_j + dz, dz the ray's offset from the
+// anchor z_m in the anchor's rotated frame) as one quotient N / P of
+// polynomials in dz, with N = sum_j K_j prod_{k != j} Q_k and P = prod_j Q_j:
 //   binary:  N = n0 + n1 dz,             P = p0 + dz (p1 + dz)
 //   triple:  N = n0 + dz (n1 + dz n2),   P = p0 + dz (p1 + dz (p2 + dz))
 // (coefficients formed in FP64 and rounded once).
 struct AnchorF {
-  cf ws;        // as Anchor::ws
+  cf ws;        // e^{-i th_m} (f(z_m) - w_c)
   cf n[3];      // numerator coefficients
   cf p[3];      // denominator coefficients (monic)
-  float e0;     // error bound constant part (as Anchor::e0)
+  float e0;     // error bound constant part
   float pad;
-  float lo2;    // as Anchor::lo2
-  float hi2;    // as Anchor::hi2
+  float lo2;    // below: every ray of the group is inside the source (FP32 certain)
+  float hi2;    // above: every ray of the group is outside (FP32 certain)
 };
-static_assert(sizeof(AnchorF) == sizeof(Anchor), "the two views share one table");
 
 using Box = BoxT<double>;
 
@@ -158,7 +140,6 @@ struct Shared {
   double dr64, dth64;
   float dr32, dth32;
   int nanch;
-  int task_ctr;        // next (row block, theta chunk) task of the forward ray stage
   int chunk;           // columns per theta chunk
   double red[NW_MAX];
 };
@@ -175,8 +156,8 @@ struct DerShared {
   DualD cx[MAXCELL_D * 4];  // cell extremes with tangents
   BoxT<DualD> box[MAXBOX_D];  // sectors with tangents
   double wder[NW_DER][12];      // per-warp sums of the row derivatives
-  double bdist[NW_DER][6][5];   // FP64 stencil distances of up to 6 boundary points per warp
   float2 acs[MAXANCH];      // cos, sin of each anchor angle
+  float4 aA[MAXANCH];       // A_0, A_1 of each anchor (FP32)
 };
 
 // Order-preserving integer keys for signed FP32 / FP64 values.
@@ -504,22 +485,17 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   double* pt = (double*)p;       p += sizeof(double) * PMAX;
   int* queue = (int*)p;          p += sizeof(int) * QMAX;
   p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);  // 16-byte rows of the offset table
-  Anchor* anch = (Anchor*)p;     p += sizeof(Anchor) * MAXANCH;
+  AnchorF* anch = (AnchorF*)p;   p += sizeof(AnchorF) * MAXANCH;
   cf* tab = (cf*)p;              p += sizeof(cf) * (GTH_MAX + 2);  // group offsets (cos d - 1, sin d)
-  const int seg = row_segment(g.n_theta, DER);  // rays per row segment
-  float* rowbuf = (float*)p;     p += DER ? sizeof(float) * NW * (seg + 4) : 0;  // row buffers (derivative mode)
   cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
-  // boundary points: forward mode, a deferred queue per warp of (column,
-  // row) pairs; derivative mode, the indices of the current row segment's
-  // points
+  // boundary points: a deferred queue per warp of (column, row) pairs
   (void)defer;
-  int* wqueue = (int*)p;         p += sizeof(int) * NW * (!DER ? 2 * dq_entries(NL) : 64);
-  // derivative mode: its state and the per-warp ray seeds
+  int* wqueue = (int*)p;         p += sizeof(int) * NW * 2 * dq_entries(NL);
+  // derivative mode: its state
   DerShared& ds = *(DerShared*)p;  p += DER ? sizeof(DerShared) : 0;
   DualD* cdual = ds.cx;
   BoxT<DualD>* bdual = ds.box;
   double* wder = &ds.wder[0][0];
-  float* abuf = (float*)p;       // NW x (seg + 4) adjoint seeds
 
   if (tid == 0) { sh.cur_set = -1; sh.warm = 0; }
   for (int k = tid; k < K; k += NT) {
@@ -1354,7 +1330,6 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     const float sfac = (float)g.s_fac;            // sigmoid steepness of the paper's gradient rule
     float acc_s = 0.f, acc_c = 0.f;  // Kahan sum of this thread
     uint32_t st_local = 0u;
-    float* buf = rowbuf + warp * (seg + 4);
     for (int bxi = 0; bxi < sh.nbox; ++bxi) {
       const Box B = sh.box[bxi];
       if (tid == 0) {
@@ -1379,10 +1354,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         sh.mth = (NTH + sh.gth - 1) / sh.gth;
         sh.mr = (NR + sh.gr - 1) / sh.gr;
         sh.nanch = sh.mth * sh.mr;
-        sh.task_ctr = 0;
-        // forward ray stage: tasks of 32 rows (one per lane) x a theta chunk
+        // ray stage: tasks of 32 rows (one per lane) x a theta chunk
         // of an even number of columns, about 8 tasks per warp per sector
-        // (dynamic assignment)
         const int nrb = (NR + 31) >> 5;
         const int nch = max(1, (8 * NW + nrb - 1) / nrb);
         sh.chunk = min(NTH, max(16, 2 * ((NTH + 2 * nch - 1) / (2 * nch))));
@@ -1409,39 +1382,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         const float e0 = (float)(16.0 * EPS32 * (fabs(ws.x) + fabs(ws.y) + 2.0 * half));
         const double rr = (double)rho32 * (double)rho32;
         float lo2 = -1.0f, hi2 = __int_as_float(0x7f800000);
-        if constexpr (DER) {
-          Anchor an_;
-          an_.ws = ws;
-          for (int j = 0; j < NL; ++j) {
-            cd Aj = R * (zc - sh.L.a[j]);
-            an_.A[j] = tof(Aj);
-            an_.K[j] = scl(inv(an_.A[j]), sh.eps32[j]);  // FP32 suffices (relative error of the U term)
-          }
-          an_.e0 = e0;
-          an_.e1 = (float)(16.0 * EPS32 * half);
-          // the same bound for the whole group: every ray has |dz| <= half, so
-          // |U|_1 <= sqrt(2) sum_j |K_j| / (|A_j| - half); squared distances
-          // outside [lo2, hi2] are decided in FP32 for every ray of the group
-          // (a superset of the per-ray uncertain band, with slack for the FP32
-          // evaluation of that band)
-          double um = 0.0;
-          bool bounded = true;
-          for (int j = 0; j < NL; ++j) {
-            const double aa = sqrt((double)an_.A[j].x * an_.A[j].x + (double)an_.A[j].y * an_.A[j].y);
-            if (!(aa > 1.0625 * half)) bounded = false;
-            else um += sqrt((double)an_.K[j].x * an_.K[j].x + (double)an_.K[j].y * an_.K[j].y) / (aa - half);
-          }
-          const double eb = (double)an_.e0 + (double)an_.e1 * 1.4142135623730951 * um;
-          const double X = 1.01 * (2.0 * (double)rho32 * eb + eb * eb) + 8.0 * EPS32 * rr;
-          if (bounded && X < 0.5 * rr) {
-            lo2 = __double2float_rd(rr - X);
-            hi2 = __double2float_ru(rr + X);
-          }
-          an_.lo2 = lo2;
-          an_.hi2 = hi2;
-          anch[an] = an_;
-          ds.acs[an] = make_float2((float)cs, (float)sn);
-        } else {
+        {
           // U = N / P (AnchorF), coefficients from the FP64 A_j, K_j
           cd A64[NL], K64[NL];
           for (int j = 0; j < NL; ++j) {
@@ -1498,7 +1439,12 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           }
           af.lo2 = lo2;
           af.hi2 = hi2;
-          reinterpret_cast<AnchorF*>(anch)[an] = af;
+          anch[an] = af;
+          if constexpr (DER) {
+            // the adjoint's ray gradients: A_j in FP32 and the anchor angle
+            ds.aA[an] = make_float4((float)A64[0].x, (float)A64[0].y, (float)A64[1].x, (float)A64[1].y);
+            ds.acs[an] = make_float2((float)cs, (float)sn);
+          }
         }
       }
       // offsets within a theta group, (cos d - 1, sin d) with d = (o + 1/2 -
@@ -1688,20 +1634,22 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           if (DER && !(Lin || Rin) && !(fL + fR - 1.0f > 0.f)) sd_n[0] = sd_n[1] = 0, sd_c[0] = sd_c[1] = 0.f;
         return W;
       };
-      if constexpr (!DER) {
-        // ---- forward ray stage.  A warp takes a task of 32 rows (lane = row
-        // i) and a chunk [c0, c1) of theta columns, and sweeps the columns in
-        // blocks of KB (all lanes at the same column, so the group offsets
-        // and, within an r group, the anchor are shared and held in
-        // registers).  Each ray's squared distance is classified against the
-        // group's FP32 band: inside (I(d) added to the row), outside, or
-        // undecided.  The inside flags go into a per-lane bit window.  At the
-        // end of a block one warp vote covers both rare events: a ray the
-        // band left undecided (its own bound, else FP64, decides it) and a
-        // boundary point (inside with an outside neighbour), which goes to
-        // the per-warp deferred queue as (column, row).  A queue flush
+      {
+        // ---- ray stage.  A warp takes a task of 32 rows (lane = row i) and
+        // a chunk [c0, c1) of theta columns, and sweeps the columns in blocks
+        // of KB (all lanes at the same column, so the group offsets and,
+        // within an r group, the anchor are shared and held in registers).
+        // Each ray's squared distance is classified against the group's FP32
+        // band: inside (I(d) added to the row), outside, or undecided.  The
+        // inside flags go into a per-lane bit window.  At the end of a block
+        // one warp vote covers both rare events: a ray the band left
+        // undecided (its own bound, else FP64, decides it) and a boundary
+        // point (inside with an outside neighbour), which goes to the
+        // per-warp deferred queue as (column, row).  A queue flush
         // re-evaluates each point's five-ray stencil and adds I (W - 1)
-        // (Appendix A per-point rule).
+        // (Appendix A per-point rule).  The adjoint adds, for every inside
+        // ray, its seed dI/dd times the gradient of d, and the queue flush
+        // the boundary points' seeds.
         constexpr int DQ = dq_entries(NL);
         constexpr int KB = 8;  // columns per block (even: column pairs load as 16 bytes)
         int2* dq = reinterpret_cast<int2*>(wqueue + warp * 2 * DQ);
@@ -1725,7 +1673,9 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         // M_P (Horner in complex FMAs, plus the rounded coefficients) and cU
         // = 3 cP + 10 (the quotient, |P|^2, the reciprocal and the products),
         // times 2 for the FP32 evaluation of the bound.
-        auto ray_eval = [&](const AnchorF& an, float tx, float ty, float ri_, float dri_, float* eb) -> float {
+        // (dzo, dwo: optionally dz and Delta w' themselves, for the adjoint)
+        auto ray_eval = [&](const AnchorF& an, float tx, float ty, float ri_, float dri_, float* eb, cf* dzo = nullptr,
+                            cf* dwo = nullptr) -> float {
           const cf dz = mk(__fmaf_rn(ri_, tx, dri_), __fmul_rn(ri_, ty));
           cf Pq, Nq;
           if constexpr (NL == 2) {
@@ -1743,6 +1693,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           const cf V = mk(__fmaf_rn(Nq.x, Pq.x, __fmul_rn(Nq.y, Pq.y)), __fmaf_rn(Nq.y, Pq.x, -__fmul_rn(Nq.x, Pq.y)));
           const cf pv = mk(__fmaf_rn(dz.x, V.x, -__fmul_rn(dz.y, V.y)), __fmaf_rn(dz.x, V.y, __fmul_rn(dz.y, V.x)));
           const cf dw = mk(__fmaf_rn(pv.x, ip, __fadd_rn(an.ws.x, dz.x)), __fmaf_rn(-pv.y, ip, __fadd_rn(an.ws.y, dz.y)));
+          if (dzo) *dzo = dz;
+          if (dwo) *dwo = dw;
           if (eb) {
             const float md = sqrtf(abs2(dz)), aP = sqrtf(q), aU = sqrtf(abs2(V)) * ip;
             const float mn = sqrtf(abs2(an.n[0])) + md * (sqrtf(abs2(an.n[1])) + md * sqrtf(abs2(an.n[2])));
@@ -1753,6 +1705,31 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           }
           return __fmaf_rn(dw.x, dw.x, __fmul_rn(dw.y, dw.y));
         };
+        // a ray the group band left open: its own bound decides in FP32 where
+        // it can, else the FP64 distance (d2 is then replaced by its square)
+        auto decide = [&](float& d2, float eb, int irow, int lw) -> bool {
+          const float X = 1.01f * (2.0f * rho32 * eb + eb * eb) + 8.0f * EPS32 * rr32;
+          if (fabsf(d2 - rr32) > X) return d2 < rr32;
+          const double d64 = ray_distance64<NL>(sh, B, irow, lw);
+          if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
+          d2 = (float)(d64 * d64);
+          return d64 < sh.rho;
+        };
+        // any column l of row irow (wrapped; beyond a non-periodic edge: outside, +inf)
+        auto classify = [&](int gi_, float ri_, float dri_, int irow, int l, float* d2o) -> bool {
+          if (!B.periodic && (l < 0 || l >= NTH)) { *d2o = __int_as_float(0x7f800000); return false; }
+          const int lw = wrapl(l);
+          const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
+          const AnchorF& an = anf[gi_ * mth + mgrp];
+          const cf t = tab_at(lw - mgrp * gth);
+          float eb;
+          float d2 = ray_eval(an, t.x, t.y, ri_, dri_, &eb);
+          bool in = d2 < an.lo2;
+          if (!in && !(d2 > an.hi2)) in = decide(d2, eb, irow, lw);
+          *d2o = d2;
+          return in;
+        };
+        if constexpr (!DER) {
         // the anchor as broadcast pairs for two columns at once (binary)
         struct AnchorP { float2 wsx, wsy, n0x, n0y, n1x, n1y, nn1y, p0x, p0y, p1x, p1y; };
         auto pairs_of = [](const AnchorF& a) -> AnchorP {
@@ -1790,30 +1767,6 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         };
         const float2 irho22 = make_float2(irho2, irho2), one2 = make_float2(1.0f, 1.0f);
         const float2 c1f2 = make_float2(c1f, c1f), c2f2 = make_float2(c2f, c2f);
-        // a ray the group band left open: its own bound decides in FP32 where
-        // it can, else the FP64 distance (d2 is then replaced by its square)
-        auto decide = [&](float& d2, float eb, int irow, int lw) -> bool {
-          const float X = 1.01f * (2.0f * rho32 * eb + eb * eb) + 8.0f * EPS32 * rr32;
-          if (fabsf(d2 - rr32) > X) return d2 < rr32;
-          const double d64 = ray_distance64<NL>(sh, B, irow, lw);
-          if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
-          d2 = (float)(d64 * d64);
-          return d64 < sh.rho;
-        };
-        // any column l of row irow (wrapped; beyond a non-periodic edge: outside, +inf)
-        auto classify = [&](int gi_, float ri_, float dri_, int irow, int l, float* d2o) -> bool {
-          if (!B.periodic && (l < 0 || l >= NTH)) { *d2o = __int_as_float(0x7f800000); return false; }
-          const int lw = wrapl(l);
-          const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
-          const AnchorF& an = anf[gi_ * mth + mgrp];
-          const cf t = tab_at(lw - mgrp * gth);
-          float eb;
-          float d2 = ray_eval(an, t.x, t.y, ri_, dri_, &eb);
-          bool in = d2 < an.lo2;
-          if (!in && !(d2 > an.hi2)) in = decide(d2, eb, irow, lw);
-          *d2o = d2;
-          return in;
-        };
         // the queued points: one per lane, each re-evaluates its stencil
         // (rays m - 2 .. m + 2, signed squared distances, negative inside)
         auto flush_queue = [&]() {
@@ -1848,11 +1801,9 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           __syncwarp();
           dq_n = 0;
         };
-        for (;;) {
-          int task = 0;
-          if (lane == 0) task = atomicAdd(&sh.task_ctr, 1);
-          task = __shfl_sync(0xffffffffu, task, 0);
-          if (task >= ntask) break;
+        // static task order (warp, warp + NW, ...): the same sums in the same
+        // order on every run (dynamic assignment measured no faster)
+        for (int task = warp; task < ntask; task += NW) {
           const int rbk = task / nch, chk = task - rbk * nch;
           const int i = rbk * 32 + lane;
           const bool rowok = i < NR;
@@ -2014,272 +1965,288 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           }
         }
         flush_queue();
-      } else {
-      for (int i = warp; i < NR; i += NW) {
-        const int gi = i / gr;
-        const float dri = ((float)(i - gi * gr) + 0.5f - 0.5f * (float)gr) * dr32;
-        const double rc64 = B.r_lo + (gi * gr + 0.5 * gr) * sh.dr64;
-        const float ri = (float)(rc64) + dri;
-        float rowacc = 0.f;
-        // derivative mode, this lane's part of the row: sum a dd/dr_i, sum a
-        // dd/dth_l, sum a dd/dth_l (l + 1/2), then dRow/d(w_c.x, w_c.y, rho,
-        // u1, a1.x, a2.x, eps1, eps2); a = dRow/dd_l the seed of ray l
-        float pg[11];
-        if (DER)
-          for (int k = 0; k < 11; ++k) pg[k] = 0.f;
-        for (int s0 = 0; s0 < NTH; s0 += seg) {
-          const int s1 = min(s0 + seg, NTH);
-          const int lo = s0 - 2, cnt = (s1 + 2) - lo;
-          // signed squared distances of the segment's rays and a 2-ray halo
-          // (negative: inside the source; +inf: beyond a non-periodic grid
-          // edge); two independent rays per lane and iteration
-          auto ray_d2 = [&](int lw, float* d2o) -> bool {
+        } else {
+          // ---- derivative ray stage (binary lens).  Per ray with seed a =
+          // dRow/dd (dI/dd inside; the paper's sigmoid rule adds its own),
+          // the row's sums pg[k] += a dd/dq_k are taken from the ray's FP32
+          // geometry (rotated frame R = e^{-i th_m}: Q_j = A_j + dz, u =
+          // Delta w' / d, gamma = sum eps_j / Q_j^2):
+          //   dd/dz = J u, J = [[1 + g.x, -g.y], [-g.y, 1 - g.x]]
+          //   dd/dr_i = (J u) . e^{i phi},  dd/dth_l = (J u) . (i z)
+          //   dd/dw_c = -conj(R) u,  dd/da_j.x = -eps_j Re(conj(u) conj(R) Q_j^2) / |Q_j|^4
+          //   dd/deps_j = -(u . Q_j) / |Q_j|^2
+          // pg: sum a dd/dr_i, sum a dd/dth_l, sum a dd/dth_l (l + 1/2), then
+          // d/d(w_c.x, w_c.y, rho, u1, a1.x, a2.x, eps1, eps2).
+          const float eps0 = sh.eps32[0], eps1 = sh.eps32[1];
+          const bool gradrule = g.grad_rule != 0;
+          auto grad_core = [&](const cf dz, const cf dw, float tx, float ty, float ri_, float lwf, const float4 A01,
+                               const float2 cs_, float a, float* pgx) {
+            const cf Q0 = mk(A01.x + dz.x, A01.y + dz.y), Q1 = mk(A01.z + dz.x, A01.w + dz.y);
+            const float i0 = 1.0f / abs2(Q0), i1 = 1.0f / abs2(Q1);
+            const float id = rsqrtf(fmaxf(abs2(dw), 1e-37f));
+            const float ux = dw.x * id, uy = dw.y * id;
+            const cf q0 = Q0 * Q0, q1 = Q1 * Q1;
+            const cf gm = scl(cj(q0), eps0 * i0 * i0) + scl(cj(q1), eps1 * i1 * i1);
+            const float gzx = (1.0f + gm.x) * ux - gm.y * uy;
+            const float gzy = -gm.y * ux + (1.0f - gm.x) * uy;
+            const float ex = 1.0f + tx, ey = ty;
+            const float gr_ = gzx * ex + gzy * ey;
+            const float gt_ = ri_ * (gzy * ex - gzx * ey);
+            pgx[0] += a * gr_;
+            pgx[1] += a * gt_;
+            pgx[2] += a * gt_ * lwf;
+            const float ct = cs_.x, st = cs_.y;
+            pgx[3] -= a * (ct * ux - st * uy);
+            pgx[4] -= a * (st * ux + ct * uy);
+            // conj(R) Q_j^2 with conj(R) = (ct, st)
+            const cf P0 = mk(ct, st) * q0, P1 = mk(ct, st) * q1;
+            pgx[7] -= a * eps0 * (ux * P0.x + uy * P0.y) * i0 * i0;
+            pgx[8] -= a * eps1 * (ux * P1.x + uy * P1.y) * i1 * i1;
+            pgx[9] -= a * (ux * Q0.x + uy * Q0.y) * i0;
+            pgx[10] -= a * (ux * Q1.x + uy * Q1.y) * i1;
+          };
+          // a ray's seed, its value I (inside) into racc and the brightness
+          // derivatives into pgx[5], pgx[6]; the paper's gradient rule (Sec.
+          // 3.5) gives the indicator chi = Theta(x), x = (rho - d) / rho, the
+          // sigmoid derivative S s (1 - s), s = 1 / (1 + e^{-S x}), with the
+          // interior weight: seed -I S s (1 - s) / rho on d and I S s (1 - s)
+          // d / rho^2 on rho (tangents only)
+          auto seed_of = [&](bool in, float d2, float* pgx, float& racc) -> float {
+            float a = 0.f;
+            if (in) {
+              float Id, Ir, Iu;
+              racc += brightness_der(d2, &Id, &Ir, &Iu);
+              a = Id;
+              pgx[5] += Ir;
+              pgx[6] += Iu;
+            }
+            if (gradrule) {
+              const float dd_ = sqrtf(d2);
+              const float sx = sfac * (1.0f - dd_ / rho32);
+              if (fabsf(sx) < 40.0f) {
+                const float sg = 1.0f / (1.0f + __expf(-sx));
+                const float c = brightness(d2) * sfac * sg * (1.0f - sg);
+                a -= c / rho32;
+                pgx[5] += c * dd_ / (rho32 * rho32);
+              }
+            }
+            return a;
+          };
+          // ray l (any column, wrapped) of row irow: its seed a times the
+          // gradient of its distance into pgx (generic: anchor from the table)
+          auto grad_at = [&](int gi_, float ri_, float dri_, int l, float a, float* pgx) {
+            if (a == 0.f || (!B.periodic && (l < 0 || l >= NTH))) return;
+            const int lw = wrapl(l);
             const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
-            const int o = lw - mgrp * gth;
-            const Anchor& an_ = anch[gi * mth + mgrp];
-            cf t = tab_at(o);
-            cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
-            cf U;
-            if constexpr (NL == 2) {
-              cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz;
-              float n0 = abs2(Q0), n1 = abs2(Q1);
-              float ip = __fdividef(1.0f, n0 * n1);  // <= 2 ulp, inside the error bound
-              cf t0 = an_.K[0] * cj(Q0), t1 = an_.K[1] * cj(Q1);
-              U = scl(scl(t0, n1) + scl(t1, n0), ip);
-            } else {
-              cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz, Q2 = an_.A[2] + dz;
-              float n0 = abs2(Q0), n1 = abs2(Q1), n2 = abs2(Q2);
-              float n01 = n0 * n1;
-              float ip = __fdividef(1.0f, n01 * n2);
-              cf t0 = an_.K[0] * cj(Q0), t1 = an_.K[1] * cj(Q1), t2 = an_.K[2] * cj(Q2);
-              U = scl(scl(t0, n1 * n2) + scl(t1, n0 * n2) + scl(t2, n01), ip);
-            }
-            cf pz = dz * U;
-            cf dw = mk(an_.ws.x + dz.x + pz.x, an_.ws.y + dz.y - pz.y);
-            float d2 = abs2(dw);
-            float eb = fmaf(an_.e1, fabsf(U.x) + fabsf(U.y), an_.e0);
-            *d2o = d2;
-            return fabsf(d2 - rho32 * rho32) <= 2.0f * rho32 * eb + eb * eb;  // FP32 cannot decide
+            const int ai = gi_ * mth + mgrp;
+            const cf t = tab_at(lw - mgrp * gth);
+            cf dz, dw;
+            (void)ray_eval(anf[ai], t.x, t.y, ri_, dri_, nullptr, &dz, &dw);
+            grad_core(dz, dw, t.x, t.y, ri_, (float)lw + 0.5f, ds.aA[ai], ds.acs[ai], a, pgx);
           };
-          // RPL independent rays per lane and iteration (instruction-level
-          // parallelism for the dependent FP32 chains of the lens map)
-          constexpr int RPL = 2;
-          // one fill iteration, RPL rays per lane.  INNER: all 32 x RPL rays
-          // of the warp lie inside the segment and inside [0, N_theta), so
-          // none needs wrapping or the beyond-the-grid marker
-          auto fill = [&](const int m0, auto inner) {
-            constexpr bool INNER = decltype(inner)::value;
-            float a_[RPL];
-            bool u_[RPL], x_[RPL];
-            int lw_[RPL];
+          // a row's sums (v[0] = sum of I W, v[1 + k] = pg[k]) as its terms
+          // of dS_b / d(r_lo, r_hi, th_lo, width) and of H: S_b = sum_i K_i
+          // Row_i, K_i = r_i dr dth, r_i = r_lo + (i + 1/2) dr, dr = (r_hi -
+          // r_lo) / N_r, dth = width / N_theta
+          auto row_terms = [&](int irow, float ri_, const float* v, double* x) {
+            const double Rw = (double)v[0], rid = (double)ri_, drd = sh.dr64, dtd = sh.dth64;
+            const double Ki = rid * drd * dtd, fi = (irow + 0.5) / NR;
+            x[0] = Ki * v[1] * (1.0 - fi) + Rw * ((1.0 - fi) * drd * dtd - rid * dtd / NR);
+            x[1] = Ki * v[1] * fi + Rw * (fi * drd * dtd + rid * dtd / NR);
+            x[2] = Ki * v[2];
+            x[3] = Ki * v[3] / NTH + Rw * rid * drd / NTH;
 #pragma unroll
-            for (int r = 0; r < RPL; ++r) {
-              const int m = m0 + 32 * r;
-              const int l = lo + m;
-              if constexpr (INNER) {
-                x_[r] = false;
-                lw_[r] = l;
-              } else {
-                x_[r] = m >= cnt || (!B.periodic && (l < 0 || l >= NTH));
-                lw_[r] = x_[r] ? 0 : wrapl(l);
+            for (int k = 4; k < 12; ++k) x[k] = Ki * v[k];
+          };
+          auto kahan = [&](float term) {
+            const float y = term - acc_c;
+            const float tt = acc_s + y;
+            acc_c = (tt - acc_s) - y;
+            acc_s = tt;
+          };
+          // the queued boundary points: one per lane.  FP32 stencil values
+          // (the flags), FP64 stencil distances for the crossing and its
+          // derivative; the point's value I (W - 1) beyond the I the sweep
+          // added, its seed (W - 1) dI/dd, and the crossing seeds on the
+          // stencil rays; its row's terms go to the warp's sums directly
+          auto flush_queue = [&]() {
+            __syncwarp();
+            double xq[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) xq[k] = 0.0;
+            if (lane < dq_n) {
+              const int2 q_ = dq[lane];
+              const int m = q_.x, irow = q_.y;
+              const int gi_ = irow / gr;
+              const float dri_ = ((float)(irow - gi_ * gr) + 0.5f - 0.5f * (float)gr) * dr32;
+              const float ri_ = (float)(B.r_lo + (gi_ * gr + 0.5 * gr) * sh.dr64) + dri_;
+              float sv[5];
+              double dist[5];
+#pragma unroll 1
+              for (int k = 0; k < 5; ++k) {
+                const int l = m - 2 + k;
+                float d2;
+                const bool in = classify(gi_, ri_, dri_, irow, l, &d2);
+                sv[k] = in ? __int_as_float(__float_as_int(d2) | 0x80000000) : d2;
+                dist[k] = (!B.periodic && (l < 0 || l >= NTH)) ? __longlong_as_double(0x7ff0000000000000LL)
+                                                               : ray_distance64<NL>(sh, B, irow, wrapl(l));
               }
-            }
+              if (signbit(sv[2])) {
+                float Id, Ir, Iu;
+                const float I = brightness_der(-sv[2], &Id, &Ir, &Iu);
+                const float W = boundary_weight(m, sv, m, irow, dist);
+                float v[12];
 #pragma unroll
-            for (int r = 0; r < RPL; ++r) u_[r] = ray_d2(lw_[r], &a_[r]);
-#pragma unroll
-            for (int r = 0; r < RPL; ++r) {
-              const int m = m0 + 32 * r;
-              float v = a_[r] < rho32 * rho32 ? -a_[r] : a_[r];
-              if (!x_[r] && u_[r]) {
-                double d64 = ray_distance64<NL>(sh, B, i, lw_[r]);
-                if (diag_cnt) atomicAdd(&sh.cnt[2], 1);
-                float q = (float)(d64 * d64);
-                v = d64 < sh.rho ? -q : q;
-              }
-              if (v == 0.f && a_[r] < rho32 * rho32) v = -0.0f;
-              if constexpr (INNER) buf[m] = v;
-              else if (m < cnt) buf[m] = x_[r] ? __int_as_float(0x7f800000) : v;
-            }
-          };
-          for (int m0 = lane; m0 < cnt; m0 += 32 * RPL) {
-            const int mb = m0 - lane;  // first ray of the warp's iteration
-            if (mb + 32 * RPL <= cnt && lo + mb >= 0 && lo + mb + 32 * RPL <= NTH)
-              fill(m0, std::true_type{});
-            else
-              fill(m0, std::false_type{});
-          }
-          float* ab = abuf + warp * (seg + 4);
-          if (DER)
-            for (int m = lane; m < cnt; m += 32) ab[m] = 0.f;
-          __syncwarp();
-          // contribution I W of boundary point mi; derivative mode: its seeds
-          auto boundary_point = [&](int mi, const double* dist) -> float {
-            if (!DER) return brightness(-buf[mi]) * boundary_weight(mi, buf + mi - 2, lo + mi, i, dist);
-            float Id, Ir, Iu;
-            float I = brightness_der(-buf[mi], &Id, &Ir, &Iu);
-            float W = boundary_weight(mi, buf + mi - 2, lo + mi, i, dist);
-            atomicAdd(&ab[mi], W * Id);
-            pg[5] += W * Ir;
-            pg[6] += W * Iu;
-            for (int sd = 0; sd < 2; ++sd) {
-              if (!sd_n[sd]) continue;
-              const float c = I * sd_c[sd];
-              pg[5] += c;
-              for (int m = 0; m < sd_n[sd]; ++m) atomicAdd(&ab[sd_b[sd] + m], -c * sd_l[sd][m]);
-            }
-            return I * W;
-          };
-          int* wq = wqueue + warp * 64;
-          int nq = 0;
-          for (int base = 2; base < cnt - 2; base += 32) {
-            const int mi = base + lane;
-            bool inside = false, edge = false;
-            if (mi < cnt - 2) {
-              float v = buf[mi];
-              if (DER && g.grad_rule && !isinf(v)) {
-                // the paper's gradient rule (Sec. 3.5): the indicator chi =
-                // Theta(x), x = (rho - d) / rho, gets the sigmoid derivative
-                // S s (1 - s), s = 1 / (1 + e^{-S x}), with the interior
-                // weight: seed -I S s (1 - s) / rho on d, and I S s (1 - s)
-                // d / rho^2 on rho (tangents only)
-                const float dd_ = sqrtf(fabsf(v));
-                const float sx = sfac * (1.0f - dd_ / rho32);
-                if (fabsf(sx) < 40.0f) {
-                  const float sg = 1.0f / (1.0f + __expf(-sx));
-                  const float c = brightness(fabsf(v)) * sfac * sg * (1.0f - sg);
-                  atomicAdd(&ab[mi], -c / rho32);
-                  pg[5] += c * dd_ / (rho32 * rho32);
+                for (int k = 0; k < 12; ++k) v[k] = 0.f;
+                v[0] = I * (W - 1.0f);
+                v[1 + 5] += (W - 1.0f) * Ir;
+                v[1 + 6] += (W - 1.0f) * Iu;
+                grad_at(gi_, ri_, dri_, m, (W - 1.0f) * Id, v + 1);
+                for (int sd = 0; sd < 2; ++sd) {
+                  if (!sd_n[sd]) continue;
+                  const float c = I * sd_c[sd];
+                  v[1 + 5] += c;
+                  for (int k = 0; k < sd_n[sd]; ++k) grad_at(gi_, ri_, dri_, sd_b[sd] + k, -c * sd_l[sd][k], v + 1);
                 }
-              }
-              inside = signbit(v);
-              if (inside) {
-                bool Lin = signbit(buf[mi - 1]), Rin = signbit(buf[mi + 1]);
-                if (Lin && Rin) {
-                  if (DER) {
-                    float Id, Ir, Iu;
-                    rowacc += brightness_der(-v, &Id, &Ir, &Iu);
-                    atomicAdd(&ab[mi], Id);
-                    pg[5] += Ir;
-                    pg[6] += Iu;
-                  } else {
-                    rowacc += brightness(-v);
-                  }
-                } else {
-                  edge = true;
-                }
+                row_terms(irow, ri_, v, xq);
+                kahan(ri_ * v[0] * bxw);
               }
             }
-            unsigned msk = __ballot_sync(0xffffffffu, edge);
-            if (msk) {
-              int pos = nq + __popc(msk & ((1u << lane) - 1u));
-              if (edge) {
-                if (pos < 64) wq[pos] = mi;
-                else rowacc += boundary_point(mi, nullptr);
-              }
-              nq += __popc(msk);
-            }
-          }
-          __syncwarp();
-          if (DER) {
-            // the FP64 stencils of up to 6 queued points at once, one ray per lane
-            const int nqq = min(nq, 64);
-            double* bd = &ds.bdist[warp][0][0];
-            for (int q0 = 0; q0 < nqq; q0 += 6) {
-              const int ncq = min(6, nqq - q0);
-              const int pi = lane / 5, k = lane - 5 * pi;
-              if (pi < ncq) {
-                const int l2_ = lo + wq[q0 + pi] + k - 2;
-                bd[pi * 5 + k] = (!B.periodic && (l2_ < 0 || l2_ >= NTH)) ? __longlong_as_double(0x7ff0000000000000LL)
-                                                                          : ray_distance64<NL>(sh, B, i, wrapl(l2_));
-              }
-              __syncwarp();
-              if (lane < ncq) rowacc += boundary_point(wq[q0 + lane], bd + lane * 5);
-              __syncwarp();
-            }
-          } else {
-            for (int q = lane; q < min(nq, 64); q += 32) rowacc += boundary_point(wq[q], nullptr);
-          }
-          __syncwarp();
-          if (DER) {
-            // gradient of every seeded ray's distance, recomputed from its
-            // anchor (rotated frame R = e^{-i th_m}: Q_j = R (z - a_j),
-            // u = R (f(z) - w_c) / d, gamma = sum eps_j / Q_j^2):
-            //   dd/dz = J u, J = [[1 + g.x, -g.y], [-g.y, 1 - g.x]]
-            //   dd/dr_i = (J u) . e^{i phi},  dd/dth_l = (J u) . (i z)
-            //   dd/dw_c = -conj(R) u,  dd/da_j.x = -eps_j Re(conj(u) conj(R) Q_j^2) / |Q_j|^4
-            //   dd/deps_j = -(u . Q_j) / |Q_j|^2
-            for (int m = lane; m < cnt; m += 32) {
-              const float a = ab[m];
-              if (a == 0.f) continue;
-              const int lw = wrapl(lo + m);
-              const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
-              const int o = lw - mgrp * gth;
-              const Anchor& an_ = anch[gi * mth + mgrp];
-              const cf t = tab_at(o);
-              const cf dz = mk(fmaf(ri, t.x, dri), ri * t.y);
-              const cf Q0 = an_.A[0] + dz, Q1 = an_.A[1] + dz;
-              const float n0 = abs2(Q0), n1 = abs2(Q1);
-              const float i0 = 1.0f / n0, i1 = 1.0f / n1;
-              const cf U = scl(an_.K[0] * cj(Q0), i0) + scl(an_.K[1] * cj(Q1), i1);
-              const cf pz = dz * U;
-              const cf dw = mk(an_.ws.x + dz.x + pz.x, an_.ws.y + dz.y - pz.y);
-              const float id = rsqrtf(fmaxf(abs2(dw), 1e-37f));
-              const float ux = dw.x * id, uy = dw.y * id;
-              const cf c0 = cj(Q0 * Q0), c1 = cj(Q1 * Q1);
-              const cf gm = scl(c0, sh.eps32[0] * i0 * i0) + scl(c1, sh.eps32[1] * i1 * i1);
-              const float gzx = (1.0f + gm.x) * ux - gm.y * uy;
-              const float gzy = -gm.y * ux + (1.0f - gm.x) * uy;
-              const float ex = 1.0f + t.x, ey = t.y;
-              const float gr_ = gzx * ex + gzy * ey;
-              const float gt_ = ri * (gzy * ex - gzx * ey);
-              pg[0] += a * gr_;
-              pg[1] += a * gt_;
-              pg[2] += a * gt_ * ((float)lw + 0.5f);
-              const float2 cs_ = ds.acs[gi * mth + mgrp];
-              const float ct = cs_.x, st = cs_.y;
-              pg[3] -= a * (ct * ux - st * uy);
-              pg[4] -= a * (st * ux + ct * uy);
-              // conj(R) Q_j^2 with conj(R) = (ct, st)
-              const cf P0 = mk(ct, st) * (Q0 * Q0), P1 = mk(ct, st) * (Q1 * Q1);
-              pg[7] -= a * sh.eps32[0] * (ux * P0.x + uy * P0.y) * i0 * i0;
-              pg[8] -= a * sh.eps32[1] * (ux * P1.x + uy * P1.y) * i1 * i1;
-              pg[9] -= a * (ux * Q0.x + uy * Q0.y) * i0;
-              pg[10] -= a * (ux * Q1.x + uy * Q1.y) * i1;
+            // the points' row terms summed over the warp in a fixed order
+#pragma unroll 1
+            for (int k = 0; k < 12; ++k) {
+              double xs = xq[k];
+              for (int o2 = 16; o2 > 0; o2 >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o2);
+              if (lane == k) wder[warp * 12 + k] += xs;
             }
             __syncwarp();
+            dq_n = 0;
+          };
+          // static task order (warp, warp + NW, ...): every sum of the
+          // adjoint is taken in the same order on every run
+          for (int task = warp; task < ntask; task += NW) {
+            const int rbk = task / nch, chk = task - rbk * nch;
+            const int i = rbk * 32 + lane;
+            const bool rowok = i < NR;
+            const int ii = rowok ? i : NR - 1;
+            const int gi = ii / gr;
+            const float dri = ((float)(ii - gi * gr) + 0.5f - 0.5f * (float)gr) * dr32;
+            const float ri = (float)(B.r_lo + (gi * gr + 0.5 * gr) * sh.dr64) + dri;
+            const int c0 = chk * CH, c1 = min(c0 + CH, NTH);
+            float rowacc = 0.f;  // sum of I over the row's inside rays
+            float pg[11];
+#pragma unroll
+            for (int k = 0; k < 11; ++k) pg[k] = 0.f;
+            float dh;
+            unsigned win = classify(gi, ri, dri, ii, c0 - 1, &dh) ? 1u : 0u;
+            AnchorF ar;  // the current group's anchor, A_j and angle
+            float4 A01 = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 cs = make_float2(1.f, 0.f);
+            int gbase = 0;
+            auto push_bits = [&](unsigned bm, int base) {
+              while (__any_sync(0xffffffffu, bm != 0u)) {
+                const bool has = bm != 0u;
+                const int m = base - (has ? __ffs(bm) - 1 : 0);
+                bm &= bm - 1u;
+                unsigned rem = __ballot_sync(0xffffffffu, has);
+                while (rem) {
+                  if (dq_n == DQ) flush_queue();
+                  unsigned take = rem;
+                  const int room = DQ - dq_n;
+                  if (__popc(take) > room) {
+                    take = 0u;
+                    unsigned r = rem;
+                    for (int k = 0; k < room; ++k) {
+                      const unsigned low = r & (0u - r);
+                      take |= low;
+                      r ^= low;
+                    }
+                  }
+                  if (take & (1u << lane)) dq[dq_n + __popc(take & lt_mask)] = make_int2(m, i);
+                  dq_n += __popc(take);
+                  rem &= ~take;
+                }
+              }
+            };
+            auto centres = [&](int nb, bool first) -> unsigned {
+              unsigned bm = ((win & ~((win << 1) & (win >> 1))) >> 1) & ((1u << nb) - 1u);
+              if (first) bm &= ~(1u << (nb - 1));
+              return rowok ? bm : 0u;
+            };
+            // one column: value, flag and, for a decided ray, its seed and
+            // gradient; an undecided ray waits for the block end
+            auto colD = [&](int l, const cf t, bool& unc) {
+              cf dz, dw;
+              const float d2 = ray_eval(ar, t.x, t.y, ri, dri, nullptr, &dz, &dw);
+              const bool in = d2 < ar.lo2;
+              const bool u_ = !(in || d2 > ar.hi2);
+              unc = unc || u_;
+              win = (win << 1) | (in ? 1u : 0u);
+              if (!u_) {
+                const float a = seed_of(in, d2, pg, rowacc);
+                if (a != 0.f) grad_core(dz, dw, t.x, t.y, ri, (float)l + 0.5f, A01, cs, a, pg);
+              }
+            };
+            auto block_end = [&](int l0, int nb, bool first, bool unc) {
+              unsigned bm = centres(nb, first);
+              if (__any_sync(0xffffffffu, unc || bm != 0u)) {
+                if (unc) {
+                  for (int k = 0; k < nb; ++k) {
+                    const cf t = tab_at(l0 + k - gbase);
+                    float eb;
+                    cf dz, dw;
+                    float d2 = ray_eval(ar, t.x, t.y, ri, dri, &eb, &dz, &dw);
+                    if (d2 < ar.lo2 || d2 > ar.hi2) continue;
+                    const bool in = decide(d2, eb, ii, l0 + k);
+                    if (in) win |= 1u << (nb - 1 - k);
+                    const float a = seed_of(in, d2, pg, rowacc);
+                    if (a != 0.f) grad_core(dz, dw, t.x, t.y, ri, (float)(l0 + k) + 0.5f, A01, cs, a, pg);
+                  }
+                  bm = centres(nb, first);
+                }
+                push_bits(bm, l0 + nb - 2);
+              }
+            };
+            int l = c0;
+            bool first = true;
+            while (l < c1) {
+              const int mgrp = (int)__umulhi((unsigned int)l, gmagic);
+              const int ai = gi * mth + mgrp;
+              ar = anf[ai];
+              A01 = ds.aA[ai];
+              cs = ds.acs[ai];
+              gbase = mgrp * gth;
+              const int lend = min(gbase + gth, c1);
+              while (l < lend) {
+                const int nb = min(KB, lend - l);
+                bool unc = false;
+#pragma unroll 1
+                for (int k = 0; k < nb; ++k) colD(l + k, tab_at(l + k - gbase), unc);
+                block_end(l, nb, first, unc);
+                first = false;
+                l += nb;
+              }
+            }
+            win = (win << 1) | (classify(gi, ri, dri, ii, c1, &dh) ? 1u : 0u);
+            push_bits(rowok ? (((win & ~((win << 1) & (win >> 1))) >> 1) & 1u) : 0u, c1 - 1);
+            // the row's terms, summed over the warp's rows
+            double x[12];
+            float v[12];
+            v[0] = rowacc;
+#pragma unroll
+            for (int k = 0; k < 11; ++k) v[k + 1] = pg[k];
+            row_terms(ii, ri, v, x);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+              double xs = rowok ? x[k] : 0.0;
+              for (int o2 = 16; o2 > 0; o2 >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, o2);
+              if (lane == k) wder[warp * 12 + k] += xs;
+            }
+            if (rowok) kahan(ri * rowacc * bxw);
           }
+          flush_queue();
         }
-        if (DER) {
-          // row i: S_b = sum_i K_i Row_i, K_i = r_i dr dth, r_i = r_lo + (i +
-          // 1/2) dr, dr = (r_hi - r_lo) / N_r, dth = width / N_theta
-          double v[12];
-          v[0] = (double)rowacc;
-          for (int k = 0; k < 11; ++k) v[k + 1] = (double)pg[k];
-          for (int o2 = 16; o2 > 0; o2 >>= 1)
-            for (int k = 0; k < 12; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o2);
-          const double Rw = v[0], rid = (double)ri, drd = sh.dr64, dtd = sh.dth64;
-          const double Ki = rid * drd * dtd, fi = (i + 0.5) / NR;
-          double mine = 0.0;
-          #pragma unroll
-          for (int k = 0; k < 12; ++k) {
-            double x;
-            if (k == 0) x = Ki * v[1] * (1.0 - fi) + Rw * ((1.0 - fi) * drd * dtd - rid * dtd / NR);
-            else if (k == 1) x = Ki * v[1] * fi + Rw * (fi * drd * dtd + rid * dtd / NR);
-            else if (k == 2) x = Ki * v[2];
-            else if (k == 3) x = Ki * v[3] / NTH + Rw * rid * drd / NTH;
-            else x = Ki * v[k];
-            if (lane == k) mine = x;
-          }
-          if (lane < 12) wder[warp * 12 + lane] += mine;
-        }
-        // Kahan-compensated accumulation of r_i dtheta dr sum_l I W
-        float term = ri * rowacc * bxw;
-        float y = term - acc_c;
-        float tt = acc_s + y;
-        acc_c = (tt - acc_s) - y;
-        acc_s = tt;
       }
-      }  // DER row loop
       __syncthreads();
       if (DER && tid < 12) {
         double sum = 0.0;
@@ -2447,12 +2414,11 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += sizeof(cf) * NP + 4 * sizeof(float) * NP;
   b += sizeof(short) * ((NP + 7) & ~(size_t)7);
   b += 3 * ((NP + 15) & ~(size_t)15);
-  b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + 16 + sizeof(Anchor) * MAXANCH;
+  b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + 16 + sizeof(AnchorF) * MAXANCH;
   const int NW = nt / 32;
   (void)defer;
-  b += sizeof(int) * NW * (!der ? 2 * dq_entries(NL) : 64);  // per-warp boundary queues
-  const int seg = row_segment(g.n_theta, der);
-  if (der) b += sizeof(DerShared) + 2 * sizeof(float) * NW * (seg + 4);  // state, row buffers and ray seeds
+  b += sizeof(int) * NW * 2 * dq_entries(NL);  // per-warp boundary queues
+  if (der) b += sizeof(DerShared);               // derivative state
   b += sizeof(cf) * (GTH_MAX + 2);
   b += sizeof(cdf) * g.n_limb;
   return b;
