@@ -179,7 +179,9 @@ int icrs_magnification(const icrs_params* p, int S, const double* t, int E,
  *             probes, cell extremes, sector merging, rays), [13..15] running
  *             count of [0] after the theta-bin, r-range and r-bin phases
  *   points    [S][E][N_limb][N_deg][4] device float or NULL: image-limb points
- *             (r, theta, flags, FP32 error bound) after root validation
+ *             (r, theta, flags, FP32 error bound) after root validation; a
+ *             slot whose root is not an image (flags without bit 0) holds the
+ *             root's position (r, theta)
  * Same semantics and errors as icrs_magnification; the diagnostics add shared
  * memory atomics on the FP64 fallback paths and clock reads.
  */

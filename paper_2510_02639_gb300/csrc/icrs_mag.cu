@@ -69,6 +69,10 @@ constexpr float EPS32 = 5.9604645e-8f;  // 2^-24
 // to the FP64 re-solve.
 constexpr float EE_SUSPECT = 1e-6f;
 constexpr float DUP_TOL = 1e-6f;
+// Two roots of a limb point that are not images, closer than PAIR_TOL
+// max(1, |z|), send it to the FP64 re-solve as well (binary lens; the
+// point-source solver's tolerance).
+constexpr float PAIR_TOL = (float)PS_PAIR_TOL;
 
 // Meta bits of an image-limb slot.
 constexpr uint8_t M_VALID = 1, M_EXACT = 2, M_UNSURE = 4, M_CAND = 8;
@@ -827,9 +831,11 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     // Binary lens: the same FP64 re-solve takes limb points whose FP32 image
     // set is not trustworthy although its count is legal: an image whose
     // refining Newton step left a large error bound (an approximation next to
-    // a critical curve, where det J ~ 0 sends the step far away), or two
-    // slots holding the same image (two approximations that met at one root
-    // while another image was missed).  Without this check the image set, and
+    // a critical curve, where det J ~ 0 sends the step far away), two slots
+    // holding the same image (two approximations that met at one root while
+    // another image was missed), or two non-image roots within PAIR_TOL of
+    // each other (a close image pair that the FP32 polynomial rounded into a
+    // pair of false roots; seen at separations up to 5.5e-3).  Without this check the image set, and
     // so the sectors, could depend on where the iteration started.  (Triple
     // lens: images beside the small lenses have large second derivatives and
     // so large bounds, and the FP64 re-solve in the lightest lens's frame is
@@ -839,6 +845,20 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       int m = 0;
       bool suspect = false;
       float zx[N], zy[N];
+      if (NL == 2) {
+        // two roots that are not images, close together: the FP32
+        // coefficients may have turned a close image pair (a limb point just
+        // inside a fold caustic) into a pair of false roots
+        for (int j = 0; j < N; ++j) {
+          if (meta[k * N + j] & M_VALID) continue;
+          const cf a_ = phi[k * N + j];
+          for (int i2 = 0; i2 < j; ++i2) {
+            if (meta[k * N + i2] & M_VALID) continue;
+            const float tol = PAIR_TOL * fmaxf(1.0f, sqrtf(abs2(a_) + 1e-30f));
+            if (abs2(a_ - phi[k * N + i2]) <= tol * tol) suspect = true;
+          }
+        }
+      }
       for (int j = 0; j < N; ++j) {
         const int ps = k * N + j;
         if (!(meta[ps] & M_VALID)) continue;
@@ -917,8 +937,15 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       for (int ps = tid; ps < NP; ps += NT) {
         float* d = diag_pts + (o + ps) * 4;
         bool ex = meta[ps] & M_EXACT;
-        d[0] = ex ? (float)pr[pidx[ps]] : r32[ps];
-        d[1] = ex ? (float)pt[pidx[ps]] : t32[ps];
+        if (meta[ps] & M_VALID) {
+          d[0] = ex ? (float)pr[pidx[ps]] : r32[ps];
+          d[1] = ex ? (float)pt[pidx[ps]] : t32[ps];
+        } else {
+          // a root that is not an image: its position (r, theta)
+          const cd z_ = tod(phi[ps]) + sh.L.a[ll];
+          d[0] = (float)sqrt(abs2(z_));
+          d[1] = (float)atan2(z_.y, z_.x);
+        }
         d[2] = (float)meta[ps];
         d[3] = e32[ps];
       }

@@ -59,13 +59,19 @@ __device__ inline int ps_polish_validate(const Lens& L, const double* epsd, cd w
   return 1;
 }
 
+// Two rejected roots of a binary lens closer than PS_PAIR_TOL max(1, |z|)
+// make the image set untrustworthy (the ray stage's root check uses the same
+// tolerance).
+constexpr double PS_PAIR_TOL = 5e-2;
+
 // Images of the source position w.  FP32 Ehrlich-Aberth on the polynomial
 // about the lightest lens (triple: a second one about the second-lightest
 // lens for the roots nearest it), then FP64 Newton on the polynomial about
 // each root's nearest lens and validation against img_tol in that frame.  If
 // that image set is not trustworthy (an illegal count, a Newton polish that
-// did not converge, or two roots that polish to the same image: FP32
-// approximations that met at one root of a close cluster), all roots are
+// did not converge, two roots that polish to the same image: FP32
+// approximations that met at one root of a close cluster, or, binary lens,
+// two close roots that are not images), all roots are
 // solved again by FP64 Ehrlich-Aberth from the FP32 ones (their converged
 // roots validated the same way).  images (optional): [N_deg][2]
 // positions, the first m valid, the rest zero.
@@ -120,15 +126,24 @@ __device__ inline PointSource<NL> point_source_solve(const Lens L, const cd w, c
       if (nc < 2 * N) cand[nc++] = z0;
     }
   }
-  cd img[N];
+  cd img[N], rej[2 * N];
   double dets[N];
-  int m = 0;
+  int m = 0, nr = 0;
   bool trust = true;
   for (int j = 0; j < nc; ++j) {
     cd zi;
     double det;
     int conv;
-    if (!ps_polish_validate<NL>(L, epsd, w, cand[j], img_tol, &zi, &det, &conv)) continue;
+    if (!ps_polish_validate<NL>(L, epsd, w, cand[j], img_tol, &zi, &det, &conv)) {
+      // binary lens: two rejected roots close together may be a close image
+      // pair that the FP32 polynomial rounded into a pair of false roots
+      if (NL == 2) {
+        for (int i = 0; i < nr; ++i)
+          if (abs2(cand[j] - rej[i]) <= PS_PAIR_TOL * PS_PAIR_TOL * fmax(1.0, abs2(cand[j]))) trust = false;
+        rej[nr++] = cand[j];
+      }
+      continue;
+    }
     if (!conv) trust = false;
     for (int i = 0; i < m; ++i)
       if (abs2(zi - img[i]) <= 1e-18 * fmax(1.0, abs2(zi))) trust = false;

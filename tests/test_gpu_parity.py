@@ -298,6 +298,36 @@ def test_interval_first_edge_epochs(G):
     assert_status(st, so, what="interval first-edge epochs")
 
 
+def test_near_critical_pair_epochs(G):
+    """Four epochs of the 5000 x 2000 scoring batch with a limb point just
+    inside a fold caustic, whose close image pair (up to 2.6e-2 apart) the
+    FP32 polynomial can round into a pair of false roots
+    (tests/golden/near_critical_epochs.json, oracle values).  Each epoch
+    cold (one launch, one set per epoch) and at the end of its light curve
+    run from the first epoch (the set repeated once per SM, so that every
+    block runs the whole curve in order with warm-started roots): both
+    against the stored oracle value at 1e-5 with the same status bits."""
+    import json
+    import os
+    import torch
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "near_critical_epochs.json")
+    gold = json.load(open(path))
+    params, t = I.binary_batch(**gold["batch"])
+    rows = gold["epochs"]
+    g = I.grid(**gold["grid"])
+    Ao = np.array([[r["A"]] for r in rows])
+    so = np.array([[r["status"]] for r in rows])
+    A, st = run_gpu(G, [params[r["set"]] for r in rows], np.array([[t[r["set"], r["epoch"]]] for r in rows]), g)
+    assert_parity(A, Ao, what="near-critical epochs, cold")
+    assert_status(st, so, what="near-critical epochs, cold")
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    for r, a_o, s_o in zip(rows, Ao[:, 0], so[:, 0]):
+        s_, e = r["set"], r["epoch"]
+        Aw, sw = run_gpu(G, [params[s_]] * nsm, np.tile(t[s_, :e + 1], (nsm, 1)), g)
+        assert_parity(Aw[:, e:e + 1], np.full((nsm, 1), a_o), what=f"near-critical epoch {s_}/{e}, warm")
+        assert_status(sw[:, e:e + 1], np.full((nsm, 1), s_o), what=f"near-critical epoch {s_}/{e}, warm")
+
+
 def test_triple_at_qualified_grid(G):
     """The triple-lens curve (rho = 5e-4) at 1024 x 2048 with N_limb = 500 (it
     fits in shared memory since the per-sector offset table holds at most

@@ -301,6 +301,42 @@ def test_sectors_cover_images_next_to_an_interval_edge(oracle_mod):
         assert np.all(cov), (row["set"], row["epoch"], int((~cov).sum()))
 
 
+def test_close_image_pairs_against_newton(oracle_mod):
+    """At the epochs of tests/golden/near_critical_epochs.json, the limb
+    point whose two closest images are nearest each other (just inside a
+    fold caustic): the oracle's images are all the solutions of the lens
+    equation that damped 2-D Newton from many starts finds (no polynomial
+    involved), each within 1e-7."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "near_critical_epochs.json")
+    gold = json.load(open(path))
+    params, t = I.binary_batch(**gold["batch"])
+    g = I.grid(**gold["grid"])
+    K = int(g["n_limb"])
+    for row in gold["epochs"]:
+        p, tt = params[row["set"]], float(t[row["set"], row["epoch"]])
+        lp = oracle_mod.limb_points(p, tt, g)
+        best, kb = np.inf, -1
+        for k in range(K):
+            v = lp[k, :, 2] > 0
+            if v.sum() < 2:
+                continue
+            z = lp[k, v, 0] * np.exp(1j * lp[k, v, 1])
+            d = np.abs(z[:, None] - z[None, :]) + np.eye(len(z)) * 1e9
+            if d.min() < best:
+                best, kb = float(d.min()), k
+        v = lp[kb, :, 2] > 0
+        zo = lp[kb, v, 0] * np.exp(1j * lp[kb, v, 1])
+        eps, a = oracle_mod.lens(p)
+        wc = oracle_mod.source_centre(p, tt)[0]
+        w = wc + p["rho"] * np.exp(2j * np.pi * kb / K)
+        sols = CF.newton_images(eps, a, w, n_start=3000)
+        assert len(sols) == len(zo), (row["set"], row["epoch"], kb, len(sols), len(zo))
+        for z in zo:
+            assert np.min(np.abs(sols - z)) < 1e-7
+
+
 def test_forward_mode_matches_fd(oracle_mod):
     """(vii) The oracle's 8-direction forward-mode derivative equals central
     finite differences of its own primal.  The primal is piecewise smooth
