@@ -669,6 +669,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         if (NL == 3 && nj == l2) continue;
         cz[nc] = z[j]; cfm[nc] = (signed char)ll; ++nc;
       }
+      int n1 = nc;  // candidates from the first frame
       if (NL == 3) {
         for (int j = 0; j < N; ++j) {
           int nj = l2;
@@ -681,6 +682,22 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           if (nj != l2) continue;
           cz[nc] = z2[j]; cfm[nc] = (signed char)l2; ++nc;
         }
+      }
+      // The two frames can disagree about which roots lie nearest the
+      // second light lens (a root by a cell boundary, kept from both): drop
+      // the first-frame candidate closest to a second-frame one, which
+      // resolves that cluster better, until N remain.
+      while (NL == 3 && nc > N && n1 > 0) {
+        int bi = 0;
+        float bd = __int_as_float(0x7f800000);
+        for (int i = 0; i < n1; ++i)
+          for (int j = n1; j < nc; ++j) {
+            const float d = abs2(cz[i] - (cz[j] + sh.aj32[ll][l2]));
+            if (d < bd) { bd = d; bi = i; }
+          }
+        for (int i = bi; i < nc - 1; ++i) { cz[i] = cz[i + 1]; cfm[i] = cfm[i + 1]; }
+        --nc;
+        --n1;
       }
       if (nc > N) { atomicOr(&sh.status, ICRS_ST_OVERFLOW); nc = N; }
       const float img_tol = (float)g.img_tol;
