@@ -276,7 +276,11 @@ int icrs_marginal_nll_grad(const icrs_params* p, int S, const double* t, int E,
  * Other entries are left untouched, and an index outside [0, S * E) is
  * skipped.  This runs the epochs that the surrogate's gate routes back to
  * ICRS.  Consecutive items of one set reuse the previous item's roots as
- * starting values, so the listed order matters for speed only.
+ * starting values.  The image sets and sectors do not depend on those
+ * starting values beyond their rounding, so the listed order changes the
+ * result by a few parts per million at most (measured: 5e-6 relative on
+ * 1.2 million routed epochs against the full launch) and changes the
+ * speed.
  *   items  [n] device int32; the other arguments are as icrs_magnification
  */
 int icrs_magnification_indexed(const icrs_params* p, int S, const double* t, int E,
