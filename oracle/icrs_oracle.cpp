@@ -98,12 +98,12 @@ typedef Cx<double> C;
 
 // ----------------------------------------------------------------------------
 // Inputs (flat arrays so the Python side needs no shared struct definition).
-// params[15] = t0, tE, u0, alpha, rho, u1, n_lens, s, q, q2, q3, s2, s3, psi,
-//              u2
+// params[19] = t0, tE, u0, alpha, rho, u1, n_lens, s, q, q2, q3, s2, s3, psi,
+//              u2, a1, a2, a3, a4
 // grid[13]   = n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter,
 //              uniform, delta_c, margin, img_tol, ld_split, grad_rule, s_fac
 // ----------------------------------------------------------------------------
-const int NPRM = 15;  // slots of one parameter set
+const int NPRM = 19;  // slots of one parameter set
 struct Grid {
   int n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter, uniform, ld_split, grad_rule;
   double delta_c, margin, img_tol, s_fac;
@@ -423,13 +423,17 @@ double point_source(const Lens<double>& L, C w, const Grid& G, uint32_t* st, C* 
 // Parameters -> trajectory (Sec. 3.5 parameter list; Fig. 3 for the angle).
 // READING: w_c = tau (cos a, sin a) + u0 (-sin a, cos a), tau = (t - t0)/tE.
 // ----------------------------------------------------------------------------
-template <class T> struct Par { T t0, tE, u0, alpha, s, q, rho, u1; double u2; };
+// Brightness-profile coefficients beyond u1 (not differentiated).
+struct Prof { double u2; double a[4]; };
+template <class T> struct Par { T t0, tE, u0, alpha, s, q, rho, u1; Prof pf; };
 
 template <class T> Par<T> par_from(const double* p, bool seed);
 template <> Par<double> par_from<double>(const double* p, bool) {
   Par<double> P;
   P.t0 = p[0]; P.tE = p[1]; P.u0 = p[2]; P.alpha = p[3]; P.rho = p[4]; P.u1 = p[5];
-  P.s = p[7]; P.q = p[8]; P.u2 = p[14];
+  P.s = p[7]; P.q = p[8];
+  P.pf.u2 = p[14];
+  for (int k = 0; k < 4; ++k) P.pf.a[k] = p[15 + k];
   return P;
 }
 template <> Par<Dual> par_from<Dual>(const double* p, bool) {
@@ -442,7 +446,8 @@ template <> Par<Dual> par_from<Dual>(const double* p, bool) {
   P.q = Dual(p[8]); P.q.d[5] = 1.0;
   P.rho = Dual(p[4]); P.rho.d[6] = 1.0;
   P.u1 = Dual(p[5]); P.u1.d[7] = 1.0;
-  P.u2 = p[14];
+  P.pf.u2 = p[14];
+  for (int k = 0; k < 4; ++k) P.pf.a[k] = p[15 + k];
   return P;
 }
 
@@ -782,28 +787,47 @@ T fdelta(const T& delta, const Grid& G) {
 }
 
 // Limb darkening (Appendix A.2 gives the linear law; the quadratic law adds
-// the next term in (1 - mu), mu = sqrt(1 - rt^2)):
-//   I(rt) = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2],
-//   I0 = 1 / (pi (1 - u1/3 - u2/6))   (= 3 / (pi (3 - u1)) for u2 = 0,
-// the normalisation of Appendix A.2: the total flux is 1); uniform: 1/pi.
+// the next term in (1 - mu), mu = sqrt(1 - rt^2); the paper's "arbitrary
+// profiles" are read as the power series in mu^(1/2) of the four-coefficient
+// law, each term normalised like the others):
+//   I(rt) = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2 - sum_k a_k (1 - mu^(k/2))],
+//   I0 = 1 / (pi (1 - u1/3 - u2/6 - sum_k a_k k/(k+4)))
+// (int_0^1 (1 - mu^(k/2)) 2 rt drt = k/(k+4); = 3 / (pi (3 - u1)) for the
+// linear law, the normalisation of Appendix A.2: the total flux is 1);
+// uniform: 1/pi.
 template <class T>
-T brightness(const T& rt2, const T& u1, double u2, const Grid& G) {
+T norm_I0(const T& u1, const Prof& pf) {
+  double sa = 0.0;
+  for (int k = 1; k <= 4; ++k) sa += pf.a[k - 1] * (double)k / (double)(k + 4);
+  return 1.0 / (PI * (1.0 - u1 / 3.0 - pf.u2 / 6.0 - sa));
+}
+template <class T>
+T brightness(const T& rt2, const T& u1, const Prof& pf, const Grid& G) {
   if (G.uniform) return T(1.0 / PI);
-  T I0 = 1.0 / (PI * (1.0 - u1 / 3.0 - u2 / 6.0));
+  T I0 = norm_I0(u1, pf);
   T one = T(1.0);
   T x = one - rt2;
   if (val(x) < 0) x = T(0.0);
-  T om = one - sqrt(x);
-  return I0 * (one - u1 * om - u2 * (om * om));
+  T mu = sqrt(x);
+  T om = one - mu;
+  T I = one - u1 * om - pf.u2 * (om * om);
+  if (pf.a[0] != 0.0 || pf.a[1] != 0.0 || pf.a[2] != 0.0 || pf.a[3] != 0.0) {
+    T sq = sqrt(mu);  // mu^(1/2)
+    T pw = one;
+    for (int k = 1; k <= 4; ++k) {
+      pw = pw * sq;
+      I = I - pf.a[k - 1] * (one - pw);
+    }
+  }
+  return I0 * I;
 }
 
 // The same law at the limb (mu = 0): the part of I that jumps to zero across
 // the source edge.
 template <class T>
-T brightness_limb(const T& u1, double u2, const Grid& G) {
+T brightness_limb(const T& u1, const Prof& pf, const Grid& G) {
   if (G.uniform) return T(1.0 / PI);
-  T I0 = 1.0 / (PI * (1.0 - u1 / 3.0 - u2 / 6.0));
-  return I0 * (1.0 - u1 - u2);
+  return norm_I0(u1, pf) * (1.0 - u1 - pf.u2 - pf.a[0] - pf.a[1] - pf.a[2] - pf.a[3]);
 }
 
 // Integral over one sector: sum_i A_i dr with
@@ -822,7 +846,7 @@ T brightness_limb(const T& u1, double u2, const Grid& G) {
 // linear fit (flag EDGE).
 template <class T>
 T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& rho,
-                  const T& u1, double u2, const Grid& G, uint32_t* st) {
+                  const T& u1, const Prof& pf, const Grid& G, uint32_t* st) {
   const int NR = G.n_r, NT = G.n_theta;
   T dr = (B.r_hi - B.r_lo) / (double)NR;
   T dth = B.width / (double)NT;
@@ -854,7 +878,7 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
           if (std::fabs(sx) > 40.0) continue;
           double sg = 1.0 / (1.0 + std::exp(-sx));
           double dchi = G.s_fac * sg * (1.0 - sg);
-          double Iv = val(brightness(d[l] * d[l] / rho2, u1, u2, G));
+          double Iv = val(brightness(d[l] * d[l] / rho2, u1, pf, G));
           row = row + (Iv * dchi) * (x - val(x));
         }
       }
@@ -915,9 +939,9 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
           WU = uL + uR - 1.0; if (val(WU) < 0) WU = T(0.0);
         }
       }
-      T I = brightness(d[l] * d[l] / rho2, u1, u2, G);
+      T I = brightness(d[l] * d[l] / rho2, u1, pf, G);
       if (G.ld_split && !G.uniform) {
-        T Il = brightness_limb(u1, u2, G);
+        T Il = brightness_limb(u1, pf, G);
         row = row + Il * WU + (I - Il) * W;
       } else {
         row = row + I * W;
@@ -968,7 +992,7 @@ T magnification_epoch(const double* prm, double t, const Grid& G, uint32_t* st,
   if (boxes_out) *boxes_out = boxes;
   T sum(0.0);
   for (size_t b = 0; b < boxes.size(); ++b)
-    sum = sum + sector_integral(boxes[b], L, wc, P.rho, P.u1, P.u2, G, st);
+    sum = sum + sector_integral(boxes[b], L, wc, P.rho, P.u1, P.pf, G, st);
   // A = sum_sectors A_sector / rho^2 (Appendix A.2; with I = 1/pi this is the
   // 1/(pi rho^2) normalisation of Appendix A.1).
   T A = sum / (P.rho * P.rho);
@@ -1083,7 +1107,7 @@ int orc_limb_points(const double* prm, double t, const double* grid, double* out
 }
 
 // Finite-source magnification for S parameter sets x E epochs.
-// prm[S][15], t[S][E], A[S][E], status[S][E] (optional).
+// prm[S][NPRM], t[S][E], A[S][E], status[S][E] (optional).
 void orc_magnification(const double* prm, int S, const double* t, int E, const double* grid,
                        double* A, uint32_t* status) {
   Grid G = grid_from(grid);

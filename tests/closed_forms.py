@@ -92,6 +92,40 @@ def single_lens_quadratic_ld_disk(u: float, rho: float, u1: float, u2: float, n_
     return val + tot
 
 
+def single_lens_profile_disk(u: float, rho: float, u1: float, u2: float, a, n_v: int = 200,
+                             n_limb: int = 4000) -> float:
+    """Disk with the power-series law I = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2 -
+    sum_k a_k (1 - mu^(k/2))], mu = sqrt(1 - r~^2), normalised to unit flux
+    (I0 = 1 / (pi (1 - u1/3 - u2/6 - sum_k a_k k/(k+4))), since
+    int_0^1 (1 - mu^(k/2)) 2 r~ dr~ = k/(k+4)), as a superposition of uniform
+    disks over mu:
+      A = I(mu=0) pi A_U(u, rho) + int_0^1 dI/dmu pi (1 - mu^2) A_U(u, rho sqrt(1 - mu^2)) dmu,
+    integrated in v = sqrt(mu), where dI/dmu dmu/dv = I0 [2 u1 v + 4 u2 v (1 - v^2)
+    + sum_k k a_k v^(k-1)] is smooth (the mu^(1/2) term's dI/dmu is not).
+    Gauss-Legendre in v, split where the sub-disk boundary passes the lens."""
+    a = list(a) + [0.0] * (4 - len(a))
+    sa = sum(a[k - 1] * k / (k + 4.0) for k in range(1, 5))
+    I0 = 1.0 / (np.pi * (1.0 - u1 / 3.0 - u2 / 6.0 - sa))
+    val = I0 * (1.0 - u1 - u2 - sum(a)) * np.pi * single_lens_uniform_disk(u, rho, n_limb)
+    edges = [0.0, 1.0]
+    if u < rho:
+        mu_c = np.sqrt(1.0 - (u / rho) ** 2)
+        edges = [0.0, np.sqrt(mu_c), 1.0]
+    x, wts = np.polynomial.legendre.leggauss(n_v)
+    tot = 0.0
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        vs = 0.5 * (hi - lo) * x + 0.5 * (hi + lo)
+        ww = 0.5 * (hi - lo) * wts
+        for v, wgt in zip(vs, ww):
+            mu = v * v
+            r = rho * np.sqrt(max(1.0 - mu * mu, 0.0))
+            if r <= 0:
+                continue
+            dI = I0 * (2.0 * u1 * v + 4.0 * u2 * v * (1.0 - mu) + sum(k * a[k - 1] * v ** (k - 1) for k in range(1, 5)))
+            tot += wgt * dI * np.pi * (1.0 - mu * mu) * single_lens_uniform_disk(u, r, n_limb)
+    return val + tot
+
+
 def lens_map(eps, a, z):
     """w = z - sum_i eps_i / conj(z - a_i)."""
     z = np.asarray(z, dtype=complex)

@@ -204,6 +204,38 @@ def test_quadratic_limb_darkened_disk(oracle_mod, u_over_rho, rho, u1, u2, split
     assert abs(A[0, 0] / ref - 1.0) < 1e-4, (A, ref)
 
 
+def test_power_series_law_reduces_to_quadratic():
+    """The power-series superposition integral with a = 0 is the quadratic
+    one (two different integration variables), and a pure a_2 (a_4) term is
+    the linear (quadratic-in-mu) law written another way: 1 - a (1 - mu) with
+    a_2 = u1; 1 - a_4 (1 - mu^2) = 1 - 2 a_4 (1 - mu) + a_4 (1 - mu)^2.  (To
+    1e-6: the uniform-disk integrals under both are accurate to ~1e-7.)"""
+    for u, rho in ((0.15, 0.05), (0.02, 0.05)):
+        ref = CF.single_lens_quadratic_ld_disk(u, rho, 0.4, 0.25)
+        assert CF.single_lens_profile_disk(u, rho, 0.4, 0.25, [0, 0, 0, 0]) == pytest.approx(ref, rel=1e-6)
+        assert CF.single_lens_profile_disk(u, rho, 0.0, 0.0, [0, 0.5, 0, 0]) == pytest.approx(
+            CF.single_lens_ld_disk(u, rho, 0.5), rel=1e-6)
+        assert CF.single_lens_profile_disk(u, rho, 0.0, 0.0, [0, 0, 0, 0.3]) == pytest.approx(
+            CF.single_lens_quadratic_ld_disk(u, rho, 0.6, -0.3), rel=1e-6)
+
+
+@pytest.mark.parametrize("u_over_rho,rho,a", [
+    (3.0, 0.05, (0.6, 0.0, 0.0, 0.0)), (0.5, 0.05, (0.3, 0.2, -0.1, 0.05)), (2.0, 5e-3, (0.0, 0.3, 0.2, 0.0)),
+    (1.2, 0.05, (0.8, -0.4, 0.3, -0.1))])
+def test_power_series_limb_darkened_disk(oracle_mod, u_over_rho, rho, a):
+    """(iii) The power-series law in mu^(1/2) (the four-coefficient law, read
+    as the paper's arbitrary radial profiles), with u1 = 0.2 on top,
+    single-lens limit: the per-point rule converges to the
+    superposition-of-uniform-disks integral in v = mu^(1/2), which pins the
+    law, its normalisation and the limb value."""
+    u = u_over_rho * rho
+    p = dict(far_single(rho=rho, u1=0.2), a1=a[0], a2=a[1], a3=a[2], a4=a[3])
+    g = I.grid(n_r=512, n_theta=2048, n_limb=1000)
+    A, st = oracle_mod.magnification(p, [u], g)
+    ref = CF.single_lens_profile_disk(u, rho, 0.2, 0.0, a)
+    assert abs(A[0, 0] / ref - 1.0) < 1e-4, (A, ref)
+
+
 @pytest.mark.parametrize("case", [
     dict(q=0.2, s=1.0, w=0.02 + 0.01j, uniform=1, u1=0.0),
     dict(q=0.05, s=1.3, w=0.3 - 0.05j, uniform=0, u1=0.5),
