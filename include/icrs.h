@@ -68,8 +68,15 @@ extern "C" {
  *   rho         source radius in Einstein radii (> 0)
  *   u1          linear limb-darkening coefficient (Appendix A.2)
  *   u2          quadratic limb-darkening coefficient (0: the linear law of
- *               Appendix A.2): I = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2],
- *               mu = sqrt(1 - d^2/rho^2), I0 = 1 / (pi (1 - u1/3 - u2/6))
+ *               Appendix A.2)
+ *   a1..a4      coefficients of the power series in mu^(1/2) (the
+ *               four-coefficient law; all 0: the linear or quadratic law):
+ *               I = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2 - sum_k a_k (1 - mu^(k/2))],
+ *               mu = sqrt(1 - d^2/rho^2),
+ *               I0 = 1 / (pi (1 - u1/3 - u2/6 - sum_k a_k k/(k+4)))
+ *               (unit total flux).  I must stay positive on the disk (the
+ *               caller's responsibility).  a1, a3 != 0: forward entry points
+ *               only (the derivative ones return ICRS_EUNSUPPORTED).
  *   n_lens      2 (binary) or 3 (triple)
  *   binary:     s = separation, q = m2/m1 (> 0); masses eps1 = 1/(1+q),
  *               eps2 = q/(1+q); lenses on the real axis with the primary at
@@ -85,6 +92,7 @@ typedef struct {
   double s, q;
   double q2, q3, s2, s3, psi;
   double u2;
+  double a1, a2, a3, a4;
 } icrs_params;
 
 /*
@@ -102,7 +110,7 @@ typedef struct {
  *   n_lens         see the field comment
  *   ld_split       0: the boundary points' weight f(delta) multiplies the whole
  *                  brightness (Appendix A.2); 1: split-profile rule (a
- *                  variant): the limb value I_limb = I0 (1 - u1 - u2), which
+ *                  variant): the limb value I_limb = I(mu = 0), which
  *                  jumps to zero across the edge, takes the uniform weight
  *                  f_U(delta) = delta + 1/2, and I - I_limb, which vanishes at
  *                  the edge like a square root, takes f(delta).  Forward

@@ -101,6 +101,9 @@ struct Shared {
   // ---- per parameter set
   Lens L;
   double rho, u1, u2;
+  double pa[4];        // a1..a4, the power series in mu^(1/2)
+  float c1h, c3h;      // their half-integer-power brightness coefficients (ray stage)
+  int half;            // c1h or c3h nonzero
   float eps32[3];
   cf aj32[3][3];       // [frame j][lens i]: a_i - a_j (FP32)
   cf D32[3][4], E32[3][3];  // polynomial parts in frame j (FP32)
@@ -525,6 +528,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         sh.rho = prm.rho;
         sh.u1 = prm.u1;
         sh.u2 = prm.u2;
+        sh.pa[0] = prm.a1; sh.pa[1] = prm.a2; sh.pa[2] = prm.a3; sh.pa[3] = prm.a4;
         for (int j = 0; j < NL; ++j) {
           sh.eps32[j] = (float)sh.L.eps[j];
           double eps[NL];
@@ -1360,17 +1364,30 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     if (diag_cnt && tid == 0) { long long c_ = clock64(); sh.cnt[11] = (int)min(c_ - sh.clk0, 2000000000LL); sh.clk0 = c_; }
     // ------------------------------------------------ 9. rays
     const int NR = g.n_r, NTH = g.n_theta;
-    // limb darkening I = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2], mu = sqrt(1 -
-    // d^2/rho^2), I0 = 1 / (pi (1 - u1/3 - u2/6)) (the linear law of
-    // Appendix A.2 when u2 = 0); uniform: I = 1/pi
-    const float I0 = g.uniform ? (float)(1.0 / kPi) : (float)(1.0 / (kPi * (1.0 - sh.u1 / 3.0 - sh.u2 / 6.0)));
+    // limb darkening I = I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2 - sum_k a_k (1 -
+    // mu^(k/2))], mu = sqrt(1 - d^2/rho^2), I0 = 1 / (pi (1 - u1/3 - u2/6 -
+    // sum_k a_k k/(k+4))) (the linear law of Appendix A.2 when the others are
+    // 0); uniform: I = 1/pi.  As a polynomial in s = mu^(1/2):
+    //   I = c0f + c1f mu + c2f mu^2 + s (c1h + c3h mu),
+    //   c0f = I0 (1 - u1 - u2 - sum a) (the limb value), c1f = I0 (u1 + 2 u2 +
+    //   a2), c2f = I0 (a4 - u2), c1h = I0 a1, c3h = I0 a3
+    const double sa_ = sh.pa[0] / 5.0 + sh.pa[1] * (2.0 / 6.0) + sh.pa[2] * (3.0 / 7.0) + sh.pa[3] * 0.5;
+    const double I0d = 1.0 / (kPi * (1.0 - sh.u1 / 3.0 - sh.u2 / 6.0 - sa_));
+    const float I0 = g.uniform ? (float)(1.0 / kPi) : (float)I0d;
     const float irho2 = 1.0f / (rho32 * rho32);
     const float irho = 1.0f / rho32;
     const float dcf = (float)g.delta_c;
-    // I = c0f + c1f mu + c2f mu^2: c0f = I0 (1 - u1 - u2) is the limb value
-    const float c0f = g.uniform ? I0 : (float)((double)I0 * (1.0 - sh.u1 - sh.u2));
-    const float c1f = g.uniform ? 0.f : (float)((double)I0 * (sh.u1 + 2.0 * sh.u2));
-    const float c2f = g.uniform ? 0.f : (float)(-(double)I0 * sh.u2);
+    const float c0f = g.uniform ? I0 : (float)(I0d * (1.0 - sh.u1 - sh.u2 - sh.pa[0] - sh.pa[1] - sh.pa[2] - sh.pa[3]));
+    const float c1f = g.uniform ? 0.f : (float)(I0d * (sh.u1 + 2.0 * sh.u2 + sh.pa[1]));
+    const float c2f = g.uniform ? 0.f : (float)(I0d * (sh.pa[3] - sh.u2));
+    // c1h, c3h and their flag live in shared memory: the default sweep
+    // never reads them
+    if (tid == 0) {
+      sh.c1h = g.uniform ? 0.f : (float)(I0d * sh.pa[0]);
+      sh.c3h = g.uniform ? 0.f : (float)(I0d * sh.pa[2]);
+      sh.half = (sh.c1h != 0.f || sh.c3h != 0.f) ? 1 : 0;
+    }
+    __syncthreads();
     const bool split = g.ld_split && !g.uniform;  // split-profile boundary rule
     const float sfac = (float)g.s_fac;            // sigmoid steepness of the paper's gradient rule
     float acc_s = 0.f, acc_c = 0.f;  // Kahan sum of this thread
@@ -1521,12 +1538,16 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       // I(d) = c0f + c1f mu + c2f mu^2, mu^2 = x = 1 - d^2/rho^2
       auto brightness = [&](float d2) -> float {
         const float x = fmaxf(fmaf(-d2, irho2, 1.0f), 1e-30f);
-        return fmaf(c2f, x, fmaf(c1f, x * rsqrtf(x), c0f));
+        const float mu = x * rsqrtf(x);
+        float I = fmaf(c2f, x, fmaf(c1f, mu, c0f));
+        if (sh.half) I = fmaf(sqrtf(mu), fmaf(sh.c3h, mu, sh.c1h), I);
+        return I;
       };
       // I and dI/dd, dI/drho, dI/du1 at squared distance d2:
       //   dI/dx = c1/(2 mu) + c2, dx/dd = -2 d/rho^2, dx/drho = 2 d^2/rho^3,
       //   dI/du1 = I (pi/3) I0 - I0 (1 - mu)   (dI0/du1 = (pi/3) I0^2)
-      auto brightness_der = [&](float d2, float* Id, float* Ir, float* Iu) -> float {
+      // (hc: std::true_type when the law has half-integer powers of mu)
+      auto brightness_der = [&](float d2, float* Id, float* Ir, float* Iu, auto hc) -> float {
         if (g.uniform) { *Id = 0.f; *Ir = 0.f; *Iu = 0.f; return I0; }
         // (hardware reciprocal square roots: 2^-22.9 relative, far inside
         // the derivative's tolerance)
@@ -1535,7 +1556,17 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         float sx = x * rs;
         float I = c0f + c1f * sx + c2f * x;
         float d = d2 * rsqrt_fast(fmaxf(d2, 1e-37f));
+        // k = (dI/dmu) / mu / rho^2
         float k = x > 0.f ? (c1f * rs + 2.0f * c2f) * irho2 : 0.f;
+        if constexpr (decltype(hc)::value) {
+          if (x > 0.f) {
+            // s (c1h + c3h mu): dI/dmu = c1h / (2 s) + 1.5 c3h s, s = mu^(1/2)
+            const float c1h = sh.c1h, c3h = sh.c3h;
+            const float s_ = sqrtf(sx);
+            I += s_ * (c1h + c3h * sx);
+            k += (0.5f * c1h / s_ + 1.5f * c3h * s_) * rs * irho2;
+          }
+        }
         *Id = -k * d;
         *Ir = k * d2 * irho;
         *Iu = I * (float)(kPi / 3.0) * I0 + I0 * (sx - 1.0f);
@@ -1917,8 +1948,13 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             if (first) bm &= ~(1u << (nb - 1));
             return rowok ? bm : 0u;
           };
-          // an inside ray's share of the row beyond c0f: mu (c1f + c2f mu)
-          auto add_in = [&](bool in, float mu) { sj = __fadd_rn(sj, in ? mu * fmaf(c2f, mu, c1f) : 0.0f); };
+          // an inside ray's share of the row beyond c0f: mu (c1f + c2f mu),
+          // plus s (c1h + c3h mu), s = mu^(1/2), when h (half-integer powers)
+          auto add_in = [&](bool in, float mu, bool h) {
+            float J = mu * fmaf(c2f, mu, c1f);
+            if (h) J = fmaf(mu * rsqrt_fast(mu), fmaf(sh.c3h, mu, sh.c1h), J);
+            sj = __fadd_rn(sj, in ? J : 0.0f);
+          };
           auto block_end = [&](int l0, int nb, bool first, bool unc) {
             unsigned bm = centres(nb, first);
             if (__any_sync(0xffffffffu, unc || bm != 0u)) {
@@ -1930,7 +1966,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                   if (d2 < lo2g || d2 > hi2g) continue;
                   if (decide(d2, eb, ii, l0 + k)) {
                     win |= 1u << (nb - 1 - k);
-                    add_in(true, sqrtf(fmaxf(__fmaf_rn(-d2, irho2, 1.0f), 0.0f)));
+                    add_in(true, sqrtf(fmaxf(__fmaf_rn(-d2, irho2, 1.0f), 1e-30f)), sh.half != 0);
                   }
                 }
                 bm = centres(nb, first);
@@ -1940,14 +1976,15 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             cnt += __popc(win & ((1u << nb) - 1u));
           };
           // one column: classify against the band, flag, and if inside add
-          // its mu (x > 5 u there, as d^2 < lo2 <= rho^2 (1 - 8 u))
-          auto col = [&](float tx, float ty, bool& unc) {
+          // its share (x > 5 u there, as d^2 < lo2 <= rho^2 (1 - 8 u)); hc:
+          // std::true_type with half-integer powers of mu
+          auto col = [&](float tx, float ty, bool& unc, auto hc) {
             const float d2 = ray_eval(anchor(), tx, ty, ri, dri, nullptr);
             const bool in = d2 < lo2g;
             unc = unc || !(in || d2 > hi2g);
             win = (win << 1) | (in ? 1u : 0u);
             const float x = __fmaf_rn(-d2, irho2, 1.0f);
-            add_in(in, __fmul_rn(x, rsqrt_fast(x)));
+            add_in(in, __fmul_rn(x, rsqrt_fast(x)), decltype(hc)::value);
           };
           // two columns (l, l + 1) with paired operations (binary lens); the
           // pair row t4 = (x_l, x_l+1, y_l, y_l+1)
@@ -1976,23 +2013,29 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             while (l < lend) {
               const int nb = min(KB, lend - l);
               bool unc = false;
-              if (nb == KB) {
+              // a full block, columns l + k, l + k + 1 from one 16-byte row
+              // (l + k - gbase even); hc selects the half-power terms
+              auto full_block = [&](auto hc) {
 #pragma unroll
                 for (int k = 0; k < KB; k += 2) {
-                  // columns l + k, l + k + 1 (l + k - gbase even: one 16-byte row)
                   const float4 t4 = *reinterpret_cast<const float4*>(tpf + 2 * (l + k));
                   if constexpr (NL == 2) {
                     col2(t4, unc);
                   } else {
-                    col(t4.x, t4.z, unc);
-                    col(t4.y, t4.w, unc);
+                    col(t4.x, t4.z, unc, hc);
+                    col(t4.y, t4.w, unc, hc);
                   }
                 }
+              };
+              // (half-integer powers: the scalar loop)
+              if (nb == KB && !sh.half) {
+                full_block(std::false_type{});
               } else {
 #pragma unroll 1
                 for (int k = 0; k < nb; ++k) {
                   const cf t = tab_at(l + k - gbase);
-                  col(t.x, t.y, unc);
+                  if (sh.half) col(t.x, t.y, unc, std::true_type{});
+                  else col(t.x, t.y, unc, std::false_type{});
                 }
               }
               block_end(l, nb, first, unc);
@@ -2059,11 +2102,11 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           // sigmoid derivative S s (1 - s), s = 1 / (1 + e^{-S x}), with the
           // interior weight: seed -I S s (1 - s) / rho on d and I S s (1 - s)
           // d / rho^2 on rho (tangents only)
-          auto seed_of = [&](bool in, float d2, float* pgx, float& racc) -> float {
+          auto seed_of = [&](bool in, float d2, float* pgx, float& racc, auto hc) -> float {
             float a = 0.f;
             if (in) {
               float Id, Ir, Iu;
-              racc += brightness_der(d2, &Id, &Ir, &Iu);
+              racc += brightness_der(d2, &Id, &Ir, &Iu, hc);
               a = Id;
               pgx[5] += Ir;
               pgx[6] += Iu;
@@ -2141,7 +2184,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               }
               if (signbit(sv[2])) {
                 float Id, Ir, Iu;
-                const float I = brightness_der(-sv[2], &Id, &Ir, &Iu);
+                const float I = sh.half ? brightness_der(-sv[2], &Id, &Ir, &Iu, std::true_type{})
+                                        : brightness_der(-sv[2], &Id, &Ir, &Iu, std::false_type{});
                 const float W = boundary_weight(m, sv, m, irow, dist);
                 float v[12];
 #pragma unroll
@@ -2223,7 +2267,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             };
             // one column: value, flag and, for a decided ray, its seed and
             // gradient; an undecided ray waits for the block end
-            auto colD = [&](int l, const cf t, bool& unc) {
+            auto colD = [&](int l, const cf t, bool& unc, auto hc) {
               cf dz, dw;
               const float d2 = ray_eval(ar, t.x, t.y, ri, dri, nullptr, &dz, &dw);
               const bool in = d2 < ar.lo2;
@@ -2231,7 +2275,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               unc = unc || u_;
               win = (win << 1) | (in ? 1u : 0u);
               if (!u_) {
-                const float a = seed_of(in, d2, pg, rowacc);
+                const float a = seed_of(in, d2, pg, rowacc, hc);
                 if (a != 0.f) grad_core(dz, dw, t.x, t.y, ri, (float)l + 0.5f, A01, cs, a, pg);
               }
             };
@@ -2247,7 +2291,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                     if (d2 < ar.lo2 || d2 > ar.hi2) continue;
                     const bool in = decide(d2, eb, ii, l0 + k);
                     if (in) win |= 1u << (nb - 1 - k);
-                    const float a = seed_of(in, d2, pg, rowacc);
+                    const float a = sh.half ? seed_of(in, d2, pg, rowacc, std::true_type{})
+                                            : seed_of(in, d2, pg, rowacc, std::false_type{});
                     if (a != 0.f) grad_core(dz, dw, t.x, t.y, ri, (float)(l0 + k) + 0.5f, A01, cs, a, pg);
                   }
                   bm = centres(nb, first);
@@ -2268,8 +2313,13 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               while (l < lend) {
                 const int nb = min(KB, lend - l);
                 bool unc = false;
+                if (sh.half) {
 #pragma unroll 1
-                for (int k = 0; k < nb; ++k) colD(l + k, tab_at(l + k - gbase), unc);
+                  for (int k = 0; k < nb; ++k) colD(l + k, tab_at(l + k - gbase), unc, std::true_type{});
+                } else {
+#pragma unroll 1
+                  for (int k = 0; k < nb; ++k) colD(l + k, tab_at(l + k - gbase), unc, std::false_type{});
+                }
                 block_end(l, nb, first, unc);
                 first = false;
                 l += nb;
@@ -2620,7 +2670,7 @@ using namespace icrs;
 
 extern "C" {
 
-int icrs_abi_version(void) { return 2; }
+int icrs_abi_version(void) { return 3; }
 
 void icrs_grid_default(icrs_grid* g) {
   if (!g) return;

@@ -217,6 +217,21 @@ def test_dA_quadratic_limb_darkening(G, oracle_mod):
     assert_dA(dA, dAo, "quadratic LD", Ao)
 
 
+def test_dA_power_series_profile(G, oracle_mod):
+    """The power-series law with half-integer powers (a1 = 0.3, a2 = 0.2, a3 =
+    -0.1, a4 = 0.05, u1 = 0.2): dA/dp of the adjoint against the oracle's FP64
+    forward mode on 12 epochs of the caustic-crossing curve (the a_k are not
+    derivative slots; they change I0 and dI/dd, dI/drho, dI/du1)."""
+    params, t = I.caustic_crossing_binary()
+    params = [dict(params[0], u1=0.2, a1=0.3, a2=0.2, a3=-0.1, a4=0.05)]
+    t = t[:, ::42]
+    g = I.grid()
+    A, dA, st, grad = gpu_dA(G, params, t, g)
+    Ao, dAo, so = oracle_mod.magnification_fwd(params, t, g)
+    assert np.all(np.abs(A / Ao - 1.0) <= TAU)
+    assert_dA(dA, dAo, "power-series law", Ao)
+
+
 def test_paper_gradient_rules(G, oracle_mod):
     """The paper's gradient rules (grid grad_rule = 1, s_fac = 100: sigmoid
     indicator derivative, fixed f'(delta) = 2/3) in the adjoint against the

@@ -250,6 +250,28 @@ def test_quadratic_limb_darkening_and_split_rule(G, oracle_mod):
         G.magnification_vjp(pd, tt, G.grid_from_dict(I.grid(ld_split=1), 2), torch.ones_like(tt))
 
 
+@pytest.mark.parametrize("coef", [(0.6, 0.0, 0.0, 0.0), (0.3, 0.2, -0.1, 0.05), (0.0, 0.3, 0.0, 0.2)])
+def test_power_series_profiles(G, oracle_mod, coef):
+    """The power-series law in mu^(1/2) (coefficients a1..a4 on top of u1 =
+    0.2; half-integer powers take the kernel's second sweep variant, integer
+    ones the default) on the caustic-crossing curve and on 64 batch epochs,
+    with the literal and the split-profile rules: against the oracle at 1e-5
+    with the same status bits."""
+    a = dict(a1=coef[0], a2=coef[1], a3=coef[2], a4=coef[3])
+    base, t = I.caustic_crossing_binary(n_epochs=40)
+    bp, bt = I.binary_batch()
+    sel = [(s_, e) for s_ in range(0, 64, 8) for e in range(0, 10000, 1250)]
+    cases = [([dict(base[0], u1=0.2, **a)], t),
+             ([dict(bp[s_], u1=0.2, **a) for s_, _ in sel], np.array([[bt[s_, e]] for s_, e in sel]))]
+    for split in (0, 1):
+        g = I.grid(ld_split=split)
+        for params, tt in cases:
+            A, st = run_gpu(G, params, tt, g)
+            Ao, so = oracle_mod.magnification(params, tt, g)
+            assert_parity(A, Ao, what=f"a={coef} split={split}")
+            assert_status(st, so, what=f"a={coef} split={split}")
+
+
 def test_qualification_sample_at_headline_grid(G):
     """The 512-epoch qualification sample of the batch (peak epochs, random
     epochs, small sources at moderate magnification, sources inside a
