@@ -23,7 +23,8 @@ _lib = None
 
 # Parameter vector layout used by the oracle's C entry points.
 PARAM_FIELDS = ("t0", "tE", "u0", "alpha", "rho", "u1", "n_lens",
-                "s", "q", "q2", "q3", "s2", "s3", "psi", "u2", "a1", "a2", "a3", "a4")
+                "s", "q", "q2", "q3", "s2", "s3", "psi", "u2", "a1", "a2", "a3", "a4",
+                "spot_x", "spot_y", "spot_r", "spot_c")
 GRID_FIELDS = ("n_r", "n_theta", "n_limb", "n_bins_r", "n_bins_theta",
                "max_iter", "uniform", "delta_c", "margin", "img_tol", "ld_split", "grad_rule", "s_fac")
 
@@ -120,7 +121,7 @@ def _d(a):
 
 
 def param_vector(p: dict) -> np.ndarray:
-    """Flatten a parameter dict into the oracle's 19-slot layout (absent keys: 0)."""
+    """Flatten a parameter dict into the oracle's 23-slot layout (absent keys: 0)."""
     out = np.zeros(len(PARAM_FIELDS))
     for i, k in enumerate(PARAM_FIELDS):
         out[i] = float(p.get(k, 0.0))

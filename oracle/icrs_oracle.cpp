@@ -35,6 +35,7 @@
 #include <cstring>
 #include <cstdlib>
 #include <vector>
+#include <limits>
 #include <type_traits>
 #include <algorithm>
 
@@ -98,12 +99,12 @@ typedef Cx<double> C;
 
 // ----------------------------------------------------------------------------
 // Inputs (flat arrays so the Python side needs no shared struct definition).
-// params[19] = t0, tE, u0, alpha, rho, u1, n_lens, s, q, q2, q3, s2, s3, psi,
-//              u2, a1, a2, a3, a4
+// params[23] = t0, tE, u0, alpha, rho, u1, n_lens, s, q, q2, q3, s2, s3, psi,
+//              u2, a1, a2, a3, a4, spot_x, spot_y, spot_r, spot_c
 // grid[13]   = n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter,
 //              uniform, delta_c, margin, img_tol, ld_split, grad_rule, s_fac
 // ----------------------------------------------------------------------------
-const int NPRM = 19;  // slots of one parameter set
+const int NPRM = 23;  // slots of one parameter set
 struct Grid {
   int n_r, n_theta, n_limb, n_bins_r, n_bins_theta, max_iter, uniform, ld_split, grad_rule;
   double delta_c, margin, img_tol, s_fac;
@@ -423,8 +424,10 @@ double point_source(const Lens<double>& L, C w, const Grid& G, uint32_t* st, C* 
 // Parameters -> trajectory (Sec. 3.5 parameter list; Fig. 3 for the angle).
 // READING: w_c = tau (cos a, sin a) + u0 (-sin a, cos a), tau = (t - t0)/tE.
 // ----------------------------------------------------------------------------
-// Brightness-profile coefficients beyond u1 (not differentiated).
-struct Prof { double u2; double a[4]; };
+// Brightness-profile coefficients beyond u1 (not differentiated), and a
+// circular spot: centre (sx, sy) rho from the source centre, radius sr rho,
+// brightness times (1 - sc) inside it.
+struct Prof { double u2; double a[4]; double sx, sy, sr, sc; };
 template <class T> struct Par { T t0, tE, u0, alpha, s, q, rho, u1; Prof pf; };
 
 template <class T> Par<T> par_from(const double* p, bool seed);
@@ -434,6 +437,7 @@ template <> Par<double> par_from<double>(const double* p, bool) {
   P.s = p[7]; P.q = p[8];
   P.pf.u2 = p[14];
   for (int k = 0; k < 4; ++k) P.pf.a[k] = p[15 + k];
+  P.pf.sx = p[19]; P.pf.sy = p[20]; P.pf.sr = p[21]; P.pf.sc = p[22];
   return P;
 }
 template <> Par<Dual> par_from<Dual>(const double* p, bool) {
@@ -448,6 +452,7 @@ template <> Par<Dual> par_from<Dual>(const double* p, bool) {
   P.u1 = Dual(p[5]); P.u1.d[7] = 1.0;
   P.pf.u2 = p[14];
   for (int k = 0; k < 4; ++k) P.pf.a[k] = p[15 + k];
+  P.pf.sx = p[19]; P.pf.sy = p[20]; P.pf.sr = p[21]; P.pf.sc = p[22];
   return P;
 }
 
@@ -844,6 +849,67 @@ T brightness_limb(const T& u1, const Prof& pf, const Grid& G) {
 // Neighbours beyond a non-periodic grid edge count as outside with delta = 1/2
 // (flag EDGE); a missing stencil point degrades the cubic to a quadratic, then
 // linear fit (flag EDGE).
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on the Legendre
+// recurrence from the Chebyshev-like first guess).
+inline void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-15) {
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        break;
+      }
+    }
+  }
+}
+
+// The spot's share of the unspotted flux, F_spot = int_spot I dA in units of
+// rho (the disk's flux is 1): polar quadrature about the spot centre, the
+// periodic trapezoid rule in the angle (128 nodes) and Gauss-Legendre in the
+// radius (16 nodes per panel) on panels graded geometrically toward the
+// spot's edge ([0, sr/2], [sr/2, 3 sr/4], ..., 20 halvings, then the rest),
+// where a spot that touches the limb meets the square-root profile.
+template <class T>
+T spot_flux(const T& u1, const Prof& pf, const Grid& G) {
+  std::vector<double> gx, gw;
+  gauss_legendre(16, gx, gw);
+  const int NA = 128;
+  std::vector<double> edges{0.0};
+  for (int k = 1; k <= 20; ++k) edges.push_back(pf.sr * (1.0 - std::ldexp(1.0, -k)));
+  edges.push_back(pf.sr);
+  T sum(0.0);
+  for (size_t b = 0; b + 1 < edges.size(); ++b) {
+    const double lo = edges[b], hi = edges[b + 1];
+    for (size_t i = 0; i < gx.size(); ++i) {
+      const double rr = 0.5 * (hi - lo) * gx[i] + 0.5 * (hi + lo);
+      const double wr = 0.5 * (hi - lo) * gw[i] * rr * (2.0 * PI / NA);
+      for (int j = 0; j < NA; ++j) {
+        const double ph = 2.0 * PI * j / NA;
+        const double x = pf.sx + rr * std::cos(ph), y = pf.sy + rr * std::sin(ph);
+        sum = sum + wr * brightness(T(x * x + y * y), u1, pf, G);
+      }
+    }
+  }
+  return sum;
+}
+
+// Spot (a variant beyond the paper's radial profiles; the paper names
+// starspots as a case ICRS handles by sampling): READING: each ray's
+// brightness is multiplied by (1 - sc) when its source-plane position lies
+// inside the spot, a plain midpoint decision with no sub-pixel rule at the
+// spot's edge (the paper gives none).
 template <class T>
 T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& rho,
                   const T& u1, const Prof& pf, const Grid& G, uint32_t* st) {
@@ -852,6 +918,7 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
   T dth = B.width / (double)NT;
   std::vector<T> d(NT);
   std::vector<char> chi(NT);
+  std::vector<double> fs(NT, 1.0);  // spot factor of each ray
   T total(0.0);
   T rho2 = rho * rho;
   for (int i = 0; i < NR; ++i) {
@@ -863,6 +930,10 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
       Cx<T> dw = w - wc;
       d[l] = sqrt(abs2(dw));
       chi[l] = val(d[l]) < val(rho);  // chi = Theta(rho - d), strict (Sec. 2.2)
+      if (pf.sc != 0.0) {
+        const double ex = val(dw.re) / val(rho) - pf.sx, ey = val(dw.im) / val(rho) - pf.sy;
+        fs[l] = (ex * ex + ey * ey < pf.sr * pf.sr) ? 1.0 - pf.sc : 1.0;
+      }
     }
     T row(0.0);
     if constexpr (std::is_same<T, Dual>::value) {
@@ -878,7 +949,7 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
           if (std::fabs(sx) > 40.0) continue;
           double sg = 1.0 / (1.0 + std::exp(-sx));
           double dchi = G.s_fac * sg * (1.0 - sg);
-          double Iv = val(brightness(d[l] * d[l] / rho2, u1, pf, G));
+          double Iv = val(brightness(d[l] * d[l] / rho2, u1, pf, G)) * fs[l];
           row = row + (Iv * dchi) * (x - val(x));
         }
       }
@@ -942,9 +1013,9 @@ T sector_integral(const Box<T>& B, const Lens<T>& L, const Cx<T>& wc, const T& r
       T I = brightness(d[l] * d[l] / rho2, u1, pf, G);
       if (G.ld_split && !G.uniform) {
         T Il = brightness_limb(u1, pf, G);
-        row = row + Il * WU + (I - Il) * W;
+        row = row + (Il * WU + (I - Il) * W) * fs[l];
       } else {
-        row = row + I * W;
+        row = row + I * W * fs[l];
       }
     }
     total = total + r * row;
@@ -996,6 +1067,16 @@ T magnification_epoch(const double* prm, double t, const Grid& G, uint32_t* st,
   // A = sum_sectors A_sector / rho^2 (Appendix A.2; with I = 1/pi this is the
   // 1/(pi rho^2) normalisation of Appendix A.1).
   T A = sum / (P.rho * P.rho);
+  // a spot: the unlensed flux is 1 - sc F_spot, F_spot the spot's share of
+  // the unspotted flux; it must lie inside the disk (else NaN)
+  if (P.pf.sc != 0.0) {
+    const double off = std::hypot(P.pf.sx, P.pf.sy);
+    if (!(P.pf.sr >= 0.0) || !(P.pf.sc < 1.0) || !(off + P.pf.sr <= 1.0)) {
+      A = T(std::numeric_limits<double>::quiet_NaN());
+    } else {
+      A = A / (1.0 - P.pf.sc * spot_flux(P.u1, P.pf, G));
+    }
+  }
   if (!(val(A) == val(A))) *st |= ST_NAN;
   return A;
 }

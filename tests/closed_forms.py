@@ -163,12 +163,13 @@ def newton_images(eps, a, w, n_start: int = 4000, seed: int = 0, box: float = 3.
 
 
 def brute_force_magnification(eps, a, wc, rho, u1=0.0, uniform=True, h_coarse=4e-3,
-                              box=2.6, refine=200, pad=0.5):
+                              box=2.6, refine=200, pad=0.5, weight=None):
     """Inverse-ray shooting on a Cartesian grid (independent of the polar
     sectors): a coarse pass over [-box, box]^2 finds the pixels whose rays land
     within (1 + pad) rho of the source centre; each connected bounding box is
     then sampled at pixel size rho / refine.  Surface brightness: uniform (1/pi)
-    or linear limb darkening; A = sum I h^2 / rho^2."""
+    or linear limb darkening, times weight((w - w_c) / rho) if given (not
+    renormalised); A = sum I h^2 / rho^2."""
     xs = np.arange(-box, box, h_coarse) + 0.5 * h_coarse
     X, Y = np.meshgrid(xs, xs, indexing="ij")
     Z = X + 1j * Y
@@ -188,12 +189,15 @@ def brute_force_magnification(eps, a, wc, rho, u1=0.0, uniform=True, h_coarse=4e
         fy = np.arange(y0, y1, h) + 0.5 * h
         for k in range(0, len(fx), 256):
             FX, FY = np.meshgrid(fx[k:k + 256], fy, indexing="ij")
-            dd = np.abs(lens_map(eps, a, FX + 1j * FY) - wc) / rho
+            wn = (lens_map(eps, a, FX + 1j * FY) - wc) / rho
+            dd = np.abs(wn)
             inside = dd < 1.0
             if uniform:
-                total += np.count_nonzero(inside) / np.pi
+                I = np.full(dd.shape, 1.0 / np.pi)
             else:
                 rt2 = np.where(inside, dd * dd, 0.0)
                 I = I0 * (1.0 - u1 * (1.0 - np.sqrt(1.0 - rt2)))
-                total += np.sum(I[inside])
+            if weight is not None:
+                I = I * weight(wn)
+            total += np.sum(I[inside])
     return total * h * h / (rho * rho)

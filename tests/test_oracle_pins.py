@@ -255,6 +255,50 @@ def test_brute_force_binary(oracle_mod, case):
     assert abs(A[0, 0] / ref - 1.0) < 2e-3, (A, ref)
 
 
+def test_full_disk_spot_leaves_magnification(oracle_mod):
+    """A spot covering the whole disk (centre 0, radius 1) scales every ray
+    and the unlensed flux alike: the magnification is the unspotted one
+    (which pins the spot flux's normalisation, F_spot = 1)."""
+    p = I.binary(q=1e-3, s=1.0, rho=1e-2, u1=0.5, u0=0.005, alpha=0.5)
+    t = np.linspace(-0.05, 0.05, 5)
+    A0, _ = oracle_mod.magnification(p, t, G)
+    A1, _ = oracle_mod.magnification(dict(p, spot_x=0.0, spot_y=0.0, spot_r=1.0, spot_c=0.6), t, G)
+    np.testing.assert_allclose(A1, A0, rtol=1e-10)
+
+
+@pytest.mark.parametrize("spot", [(0.3, -0.2, 0.4, 0.7), (-0.5, 0.1, 0.3, 0.5)])
+def test_spot_brute_force(oracle_mod, spot):
+    """A spotted, linearly limb-darkened source, single-lens limit and a
+    binary: the oracle agrees with Cartesian inverse-ray shooting weighted by
+    the spot, normalised by a brute-force sum of the spotted disk's flux on a
+    fine grid (independent of the oracle's spot-flux quadrature), to the brute
+    force's pixel error."""
+    sx, sy, sr, sc = spot
+    rho, u1 = 0.05, 0.5
+    spot_d = dict(spot_x=sx, spot_y=sy, spot_r=sr, spot_c=sc)
+
+    def weight(wn):
+        return np.where(np.abs(wn - (sx + 1j * sy)) < sr, 1.0 - sc, 1.0)
+
+    # unlensed flux of the spotted disk, relative to the unspotted one
+    n = 4000
+    xs = (np.arange(n) + 0.5) / n * 2.0 - 1.0
+    X, Y = np.meshgrid(xs, xs, indexing="ij")
+    R2 = X * X + Y * Y
+    ins = R2 < 1.0
+    Ild = 1.0 - u1 * (1.0 - np.sqrt(np.where(ins, 1.0 - R2, 0.0)))
+    flux = np.sum((Ild * weight(X + 1j * Y))[ins]) / np.sum(Ild[ins])
+    for q, s_, w in ((1e-10, 20.0, 0.08 + 0.0j), (0.05, 1.3, 0.3 - 0.05j)):
+        p = dict(I.binary(q=q, s=s_, rho=rho, u1=u1, t0=0.0, tE=1.0, u0=w.imag, alpha=0.0), **spot_d)
+        g = I.grid(n_r=200, n_theta=800)
+        A, st = oracle_mod.magnification(p, [w.real], g)
+        eps, a = oracle_mod.lens(p)
+        wc = oracle_mod.source_centre(p, [w.real])[0]
+        ref = CF.brute_force_magnification(eps, a, wc, rho, u1=u1, uniform=False, refine=120,
+                                           weight=weight) / flux
+        assert abs(A[0, 0] / ref - 1.0) < 2e-3, (A, ref, q)
+
+
 def test_mirror_symmetry(oracle_mod):
     """(vi) Both lenses lie on the real axis, so the map commutes with complex
     conjugation: (alpha, u0) -> (-alpha, -u0) conjugates every source position
