@@ -75,8 +75,16 @@ extern "C" {
  *               mu = sqrt(1 - d^2/rho^2),
  *               I0 = 1 / (pi (1 - u1/3 - u2/6 - sum_k a_k k/(k+4)))
  *               (unit total flux).  I must stay positive on the disk (the
- *               caller's responsibility).  a1, a3 != 0: forward entry points
- *               only (the derivative ones return ICRS_EUNSUPPORTED).
+ *               caller's responsibility).
+ *   spot_x, spot_y, spot_r, spot_c
+ *               a circular spot (spot_c = 0: none): centre (spot_x, spot_y)
+ *               rho from the source centre (lens-plane axes), radius spot_r
+ *               rho, brightness times (1 - spot_c) inside it; the spot must
+ *               lie inside the disk (hypot(spot_x, spot_y) + spot_r <= 1,
+ *               0 <= spot_r, spot_c < 1), else A is NaN with ICRS_ST_NAN.
+ *               A ray inside the spot is weighted by (1 - spot_c) (no
+ *               sub-pixel rule at the spot's edge); the unlensed flux is
+ *               1 - spot_c F_spot (F_spot by quadrature).
  *   n_lens      2 (binary) or 3 (triple)
  *   binary:     s = separation, q = m2/m1 (> 0); masses eps1 = 1/(1+q),
  *               eps2 = q/(1+q); lenses on the real axis with the primary at
@@ -93,6 +101,7 @@ typedef struct {
   double q2, q3, s2, s3, psi;
   double u2;
   double a1, a2, a3, a4;
+  double spot_x, spot_y, spot_r, spot_c;
 } icrs_params;
 
 /*

@@ -104,6 +104,11 @@ struct Shared {
   double pa[4];        // a1..a4, the power series in mu^(1/2)
   float c1h, c3h;      // their half-integer-power brightness coefficients (ray stage)
   int half;            // c1h or c3h nonzero
+  // spot: centre (rho units), radius^2 and contrast; 1 / (1 - c F_spot) and
+  // its u1 derivative over itself times c F_spot' ... (see the chain);
+  // spot_new: the set changed and has a spot; generic: half or spot
+  double spot_x, spot_y, spot_r, spot_c, spot_norm, spot_gu, spot_acc[2];
+  int spot, spot_bad, spot_new, generic;
   float eps32[3];
   cf aj32[3][3];       // [frame j][lens i]: a_i - a_j (FP32)
   cf D32[3][4], E32[3][3];  // polynomial parts in frame j (FP32)
@@ -265,10 +270,21 @@ __device__ inline int validate_root64(const Shared& sh, cd z0, cd w, double img_
   return 1;
 }
 
-// FP64 distance of ray (i, l) of a sector from the source centre, with the
-// grid of Sec. 3.3: r_i = r_lo + (i + 1/2) dr, th_l = th_lo + (l + 1/2) dth.
+// FP64 offset of ray (i, l) of a sector from the source centre (and its
+// distance below), with the grid of Sec. 3.3: r_i = r_lo + (i + 1/2) dr,
+// th_l = th_lo + (l + 1/2) dth.  Out of line: these are the rare fallbacks,
+// and inlined they cost the ray sweeps registers.
 template <int NL>
-__device__ inline double ray_distance64(const Shared& sh, const Box& B, int i, int l) {
+__device__ __noinline__ cd ray_offset64(const Shared& sh, const Box& B, int i, int l) {
+  double r = B.r_lo + (i + 0.5) * sh.dr64;
+  double th = B.th_lo + (l + 0.5) * sh.dth64;
+  double s, c;
+  sincos(th, &s, &c);
+  cd z = mk(r * c, r * s);
+  return lens_map<NL, double>(sh.L.eps, sh.L.a, z) - sh.wc;
+}
+template <int NL>
+__device__ __noinline__ double ray_distance64(const Shared& sh, const Box& B, int i, int l) {
   double r = B.r_lo + (i + 0.5) * sh.dr64;
   double th = B.th_lo + (l + 0.5) * sh.dth64;
   double s, c;
@@ -493,6 +509,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   int* queue = (int*)p;          p += sizeof(int) * QMAX;
   p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);  // 16-byte rows of the offset table
   AnchorF* anch = (AnchorF*)p;   p += sizeof(AnchorF) * MAXANCH;
+  float2* spc = (float2*)p;      p += sizeof(float2) * MAXANCH;  // spot centre in each anchor's frame
   cf* tab = (cf*)p;              p += sizeof(cf) * (GTH_MAX + 2);  // group offsets (cos d - 1, sin d)
   cdf* ulimb = (cdf*)p;          p += sizeof(cdf) * K;   // e^{2 pi i k / N_limb} as double-float
   // boundary points: a deferred queue per warp of (column, row) pairs
@@ -529,6 +546,14 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         sh.u1 = prm.u1;
         sh.u2 = prm.u2;
         sh.pa[0] = prm.a1; sh.pa[1] = prm.a2; sh.pa[2] = prm.a3; sh.pa[3] = prm.a4;
+        sh.spot = prm.spot_c != 0.0;
+        sh.spot_x = prm.spot_x; sh.spot_y = prm.spot_y; sh.spot_r = prm.spot_r; sh.spot_c = prm.spot_c;
+        sh.spot_bad = sh.spot && !(prm.spot_r >= 0.0 && prm.spot_c < 1.0 &&
+                                   hypot(prm.spot_x, prm.spot_y) + prm.spot_r <= 1.0);
+        sh.spot_new = sh.spot && !sh.spot_bad;
+        sh.spot_norm = 1.0;
+        sh.spot_gu = 0.0;
+        sh.spot_acc[0] = sh.spot_acc[1] = 0.0;
         for (int j = 0; j < NL; ++j) {
           sh.eps32[j] = (float)sh.L.eps[j];
           double eps[NL];
@@ -556,6 +581,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         sh.cur_set = s;
       } else {
         sh.warm = 1;  // previous tile of this block was the previous epoch of this set
+        sh.spot_new = 0;
       }
       sh.wc = source_centre(P[s], T_[(size_t)s * E + e]);
       if (DER) {
@@ -595,6 +621,64 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     __syncthreads();
     const int ll = sh.L.ll;
     const float rho32 = (float)sh.rho;
+    if (sh.spot_new) {
+      // the spot's share of the unspotted flux F_spot = int_spot I dA (rho
+      // units, the disk's flux is 1) and dF_spot/du1, once per set: polar
+      // quadrature about the spot centre, the periodic trapezoid rule in the
+      // angle (64 nodes), 8-point Gauss-Legendre in the radius on 16 panels
+      // graded geometrically toward the spot's edge
+      double gx[8], gw[8];
+      for (int i = 0; i < 8; ++i) {
+        double z = cos(kPi * (i + 0.75) / 8.5), dp = 1.0;
+        for (int it = 0; it < 60; ++it) {
+          double p0 = 1.0, p1 = z;
+          for (int k = 2; k <= 8; ++k) { const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k; p0 = p1; p1 = p2; }
+          dp = 8.0 * (z * p1 - p0) / (z * z - 1.0);
+          const double dz = p1 / dp;
+          z -= dz;
+          if (fabs(dz) < 1e-15) break;
+        }
+        gx[i] = z;
+        gw[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+      }
+      const double sa = sh.pa[0] / 5.0 + sh.pa[1] * (2.0 / 6.0) + sh.pa[2] * (3.0 / 7.0) + sh.pa[3] * 0.5;
+      const double I0d = g.uniform ? 1.0 / kPi : 1.0 / (kPi * (1.0 - sh.u1 / 3.0 - sh.u2 / 6.0 - sa));
+      double f = 0.0, fu = 0.0;
+      for (int idx = tid; idx < 16 * 8 * 64; idx += NT) {
+        const int b = idx / 512, i = (idx / 64) & 7, j = idx & 63;
+        const double lo = b == 0 ? 0.0 : sh.spot_r * (1.0 - ldexp(1.0, -b));
+        const double hi = b == 15 ? sh.spot_r : sh.spot_r * (1.0 - ldexp(1.0, -(b + 1)));
+        const double rr = 0.5 * (hi - lo) * gx[i] + 0.5 * (hi + lo);
+        const double w_ = 0.5 * (hi - lo) * gw[i] * rr * (2.0 * kPi / 64.0);
+        double sn_, cs_;
+        sincospi(2.0 * j / 64.0, &sn_, &cs_);
+        const double x = sh.spot_x + rr * cs_, y = sh.spot_y + rr * sn_;
+        const double mu = sqrt(fmax(1.0 - (x * x + y * y), 0.0));
+        double I = 1.0, Iu = 0.0;
+        if (!g.uniform) {
+          const double om = 1.0 - mu, sq = sqrt(mu);
+          I = 1.0 - sh.u1 * om - sh.u2 * om * om - sh.pa[0] * (1.0 - sq) - sh.pa[1] * (1.0 - mu) -
+              sh.pa[2] * (1.0 - sq * mu) - sh.pa[3] * (1.0 - mu * mu);
+          // dI/du1 = (pi/3) I0 I - I0 (1 - mu), with I = I0 x the bracket
+          Iu = (kPi / 3.0) * I0d * I0d * I - I0d * om;
+        }
+        f += w_ * I0d * I;
+        fu += w_ * Iu;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        f += __shfl_xor_sync(0xffffffffu, f, o);
+        fu += __shfl_xor_sync(0xffffffffu, fu, o);
+      }
+      if (lane == 0) { atomicAdd(&sh.spot_acc[0], f); atomicAdd(&sh.spot_acc[1], fu); }
+      __syncthreads();
+      if (tid == 0) {
+        // A = N S / rho^2, N = 1 / (1 - c F_spot): dN/du1 = N^2 c dF/du1,
+        // so dA/du1 gains A N c dF/du1 (spot_gu)
+        sh.spot_norm = 1.0 / (1.0 - sh.spot_c * sh.spot_acc[0]);
+        sh.spot_gu = sh.spot_norm * sh.spot_c * sh.spot_acc[1];
+      }
+      __syncthreads();
+    }
 
     // ------------------------------------------------ 1. limb roots (FP32 EA)
     // Cold start: 32 anchor limb points from the Cauchy circle, then every
@@ -1386,6 +1470,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       sh.c1h = g.uniform ? 0.f : (float)(I0d * sh.pa[0]);
       sh.c3h = g.uniform ? 0.f : (float)(I0d * sh.pa[2]);
       sh.half = (sh.c1h != 0.f || sh.c3h != 0.f) ? 1 : 0;
+      sh.generic = sh.half || sh.spot;
     }
     __syncthreads();
     const bool split = g.ld_split && !g.uniform;  // split-profile boundary rule
@@ -1438,6 +1523,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         cd zc = mk(rc * cs, rc * sn);
         cd wsd = lens_map<NL, double>(sh.L.eps, sh.L.a, zc) - sh.wc;
         const cf ws = tof(R * wsd);
+        if (sh.spot) spc[an] = make_float2((float)(sh.rho * (cs * sh.spot_x + sn * sh.spot_y)),
+                                           (float)(sh.rho * (cs * sh.spot_y - sn * sh.spot_x)));
         // error bound of |Delta w'|: anchor term plus rounding of the ray's
         // offset (at most the group half-diagonal) and of its image term
         const double half = 0.5 * gr * sh.dr64 + (B.r_hi) * 0.5 * gth * sh.dth64;
@@ -1546,7 +1633,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       // I and dI/dd, dI/drho, dI/du1 at squared distance d2:
       //   dI/dx = c1/(2 mu) + c2, dx/dd = -2 d/rho^2, dx/drho = 2 d^2/rho^3,
       //   dI/du1 = I (pi/3) I0 - I0 (1 - mu)   (dI0/du1 = (pi/3) I0^2)
-      // (hc: std::true_type when the law has half-integer powers of mu)
+      // (hc: std::true_type for the generic law: half-integer powers of mu
+      // checked at run time)
       auto brightness_der = [&](float d2, float* Id, float* Ir, float* Iu, auto hc) -> float {
         if (g.uniform) { *Id = 0.f; *Ir = 0.f; *Iu = 0.f; return I0; }
         // (hardware reciprocal square roots: 2^-22.9 relative, far inside
@@ -1559,7 +1647,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         // k = (dI/dmu) / mu / rho^2
         float k = x > 0.f ? (c1f * rs + 2.0f * c2f) * irho2 : 0.f;
         if constexpr (decltype(hc)::value) {
-          if (x > 0.f) {
+          if (sh.half && x > 0.f) {
             // s (c1h + c3h mu): dI/dmu = c1h / (2 s) + 1.5 c3h s, s = mu^(1/2)
             const float c1h = sh.c1h, c3h = sh.c3h;
             const float s_ = sqrtf(sx);
@@ -1795,17 +1883,41 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           return d64 < sh.rho;
         };
         // any column l of row irow (wrapped; beyond a non-periodic edge: outside, +inf)
-        auto classify = [&](int gi_, float ri_, float dri_, int irow, int l, float* d2o) -> bool {
-          if (!B.periodic && (l < 0 || l >= NTH)) { *d2o = __int_as_float(0x7f800000); return false; }
+        // a ray's spot factor: 1 - c inside the spot, else 1.  dw: the ray's
+        // offset from the source centre in the frame of anchor ai, with error
+        // bound eb; the spot centre's FP32 rounding adds 4 u rho.  Decided in
+        // FP32 outside the band, else from the FP64 offset as the oracle
+        // decides it.
+        const float spot_rr = (float)(sh.rho * sh.spot_r);
+        const float spot_r2 = spot_rr * spot_rr;
+        const float spot_f = (float)(1.0 - sh.spot_c);
+        auto spot_factor = [&](int ai, const cf dw, float eb, int irow, int lw) -> float {
+          if (!sh.spot) return 1.f;
+          const float2 c = spc[ai];
+          const float ex = dw.x - c.x, ey = dw.y - c.y;
+          const float q = fmaf(ex, ex, ey * ey);
+          const float e = eb + 4.0f * EPS32 * rho32;
+          const float X = 1.01f * (2.0f * spot_rr * e + e * e) + 8.0f * EPS32 * spot_r2;
+          if (fabsf(q - spot_r2) > X) return q < spot_r2 ? spot_f : 1.f;
+          const cd d64 = ray_offset64<NL>(sh, B, irow, lw);
+          const double fx = d64.x / sh.rho - sh.spot_x, fy = d64.y / sh.rho - sh.spot_y;
+          return fx * fx + fy * fy < sh.spot_r * sh.spot_r ? spot_f : 1.f;
+        };
+        // (fso: optionally the ray's spot factor)
+        auto classify = [&](int gi_, float ri_, float dri_, int irow, int l, float* d2o,
+                            float* fso = nullptr) -> bool {
+          if (!B.periodic && (l < 0 || l >= NTH)) { *d2o = __int_as_float(0x7f800000); if (fso) *fso = 1.f; return false; }
           const int lw = wrapl(l);
           const int mgrp = (int)__umulhi((unsigned int)lw, gmagic);
           const AnchorF& an = anf[gi_ * mth + mgrp];
           const cf t = tab_at(lw - mgrp * gth);
           float eb;
-          float d2 = ray_eval(an, t.x, t.y, ri_, dri_, &eb);
+          cf dw;
+          float d2 = ray_eval(an, t.x, t.y, ri_, dri_, &eb, nullptr, &dw);
           bool in = d2 < an.lo2;
           if (!in && !(d2 > an.hi2)) in = decide(d2, eb, irow, lw);
           *d2o = d2;
+          if (fso) *fso = spot_factor(gi_ * mth + mgrp, dw, eb, irow, lw);
           return in;
         };
         if constexpr (!DER) {
@@ -1856,11 +1968,11 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             const int gi_ = irow / gr;
             const float dri_ = ((float)(irow - gi_ * gr) + 0.5f - 0.5f * (float)gr) * dr32;
             const float ri_ = (float)(B.r_lo + (gi_ * gr + 0.5 * gr) * sh.dr64) + dri_;
-            float sv[5];
+            float sv[5], fsc = 1.f;
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
               float d2;
-              const bool in = classify(gi_, ri_, dri_, irow, m - 2 + k, &d2);
+              const bool in = classify(gi_, ri_, dri_, irow, m - 2 + k, &d2, k == 2 ? &fsc : nullptr);
               sv[k] = in ? __int_as_float(__float_as_int(d2) | 0x80000000) : d2;
             }
             if (signbit(sv[2])) {
@@ -1870,7 +1982,8 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               const float rw = ri_ * bxw;
               // literal rule: I (W - 1); split-profile rule: the limb value c0f
               // with the uniform weight, the rest with f(delta)
-              const float term = split ? rw * (c0f * (WU - 1.0f) + (I - c0f) * (W - 1.0f)) : rw * I * (W - 1.0f);
+              // (a spot scales the point's whole brightness)
+              const float term = fsc * (split ? rw * (c0f * (WU - 1.0f) + (I - c0f) * (W - 1.0f)) : rw * I * (W - 1.0f));
               const float y = term - acc_c;
               const float tt = acc_s + y;
               acc_c = (tt - acc_s) - y;
@@ -1950,9 +2063,12 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           };
           // an inside ray's share of the row beyond c0f: mu (c1f + c2f mu),
           // plus s (c1h + c3h mu), s = mu^(1/2), when h (half-integer powers)
-          auto add_in = [&](bool in, float mu, bool h) {
+          // fs: the spot factor (the count adds c0f, so a spotted ray adds
+          // fs (c0f + J) - c0f here)
+          auto add_in = [&](bool in, float mu, bool h, float fs) {
             float J = mu * fmaf(c2f, mu, c1f);
             if (h) J = fmaf(mu * rsqrt_fast(mu), fmaf(sh.c3h, mu, sh.c1h), J);
+            J = fmaf(fs, J, -c0f * (1.0f - fs));
             sj = __fadd_rn(sj, in ? J : 0.0f);
           };
           auto block_end = [&](int l0, int nb, bool first, bool unc) {
@@ -1962,11 +2078,13 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                 for (int k = 0; k < nb; ++k) {
                   const cf t = tab_at(l0 + k - gbase);
                   float eb;
-                  float d2 = ray_eval(anchor(), t.x, t.y, ri, dri, &eb);
+                  cf dw;
+                  float d2 = ray_eval(anchor(), t.x, t.y, ri, dri, &eb, nullptr, &dw);
                   if (d2 < lo2g || d2 > hi2g) continue;
                   if (decide(d2, eb, ii, l0 + k)) {
                     win |= 1u << (nb - 1 - k);
-                    add_in(true, sqrtf(fmaxf(__fmaf_rn(-d2, irho2, 1.0f), 1e-30f)), sh.half != 0);
+                    add_in(true, sqrtf(fmaxf(__fmaf_rn(-d2, irho2, 1.0f), 1e-30f)), sh.half != 0,
+                           spot_factor(aidx, dw, eb, ii, l0 + k));
                   }
                 }
                 bm = centres(nb, first);
@@ -1977,14 +2095,22 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           };
           // one column: classify against the band, flag, and if inside add
           // its share (x > 5 u there, as d^2 < lo2 <= rho^2 (1 - 8 u)); hc:
-          // std::true_type with half-integer powers of mu
-          auto col = [&](float tx, float ty, bool& unc, auto hc) {
-            const float d2 = ray_eval(anchor(), tx, ty, ri, dri, nullptr);
+          // std::true_type for the generic law (half-integer powers of mu or
+          // a spot, checked at run time)
+          auto col = [&](int l, float tx, float ty, bool& unc, auto hc) {
+            cf dw;
+            float eb = 0.f;
+            constexpr bool GEN = decltype(hc)::value;
+            const float d2 = ray_eval(anchor(), tx, ty, ri, dri, GEN ? &eb : nullptr, nullptr, GEN ? &dw : nullptr);
             const bool in = d2 < lo2g;
             unc = unc || !(in || d2 > hi2g);
             win = (win << 1) | (in ? 1u : 0u);
             const float x = __fmaf_rn(-d2, irho2, 1.0f);
-            add_in(in, __fmul_rn(x, rsqrt_fast(x)), decltype(hc)::value);
+            if constexpr (GEN)
+              add_in(in, __fmul_rn(x, rsqrt_fast(x)), sh.half != 0, in ? spot_factor(aidx, dw, eb, ii, l) : 1.0f);
+            else
+              add_in(in, __fmul_rn(x, rsqrt_fast(x)), false, 1.0f);
+            (void)l;
           };
           // two columns (l, l + 1) with paired operations (binary lens); the
           // pair row t4 = (x_l, x_l+1, y_l, y_l+1)
@@ -2022,20 +2148,20 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                   if constexpr (NL == 2) {
                     col2(t4, unc);
                   } else {
-                    col(t4.x, t4.z, unc, hc);
-                    col(t4.y, t4.w, unc, hc);
+                    col(l + k, t4.x, t4.z, unc, hc);
+                    col(l + k + 1, t4.y, t4.w, unc, hc);
                   }
                 }
               };
-              // (half-integer powers: the scalar loop)
-              if (nb == KB && !sh.half) {
+              // (the generic law, half-integer powers or a spot: the scalar loop)
+              if (nb == KB && !sh.generic) {
                 full_block(std::false_type{});
               } else {
 #pragma unroll 1
                 for (int k = 0; k < nb; ++k) {
                   const cf t = tab_at(l + k - gbase);
-                  if (sh.half) col(t.x, t.y, unc, std::true_type{});
-                  else col(t.x, t.y, unc, std::false_type{});
+                  if (sh.generic) col(l + k, t.x, t.y, unc, std::true_type{});
+                  else col(l + k, t.x, t.y, unc, std::false_type{});
                 }
               }
               block_end(l, nb, first, unc);
@@ -2102,21 +2228,22 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
           // sigmoid derivative S s (1 - s), s = 1 / (1 + e^{-S x}), with the
           // interior weight: seed -I S s (1 - s) / rho on d and I S s (1 - s)
           // d / rho^2 on rho (tangents only)
-          auto seed_of = [&](bool in, float d2, float* pgx, float& racc, auto hc) -> float {
+          // (fs: the ray's spot factor, which scales its brightness)
+          auto seed_of = [&](bool in, float d2, float* pgx, float& racc, auto hc, float fs) -> float {
             float a = 0.f;
             if (in) {
               float Id, Ir, Iu;
-              racc += brightness_der(d2, &Id, &Ir, &Iu, hc);
-              a = Id;
-              pgx[5] += Ir;
-              pgx[6] += Iu;
+              racc += fs * brightness_der(d2, &Id, &Ir, &Iu, hc);
+              a = fs * Id;
+              pgx[5] += fs * Ir;
+              pgx[6] += fs * Iu;
             }
             if (gradrule) {
               const float dd_ = sqrtf(d2);
               const float sx = sfac * (1.0f - dd_ / rho32);
               if (fabsf(sx) < 40.0f) {
                 const float sg = 1.0f / (1.0f + __expf(-sx));
-                const float c = brightness(d2) * sfac * sg * (1.0f - sg);
+                const float c = fs * brightness(d2) * sfac * sg * (1.0f - sg);
                 a -= c / rho32;
                 pgx[5] += c * dd_ / (rho32 * rho32);
               }
@@ -2171,21 +2298,23 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               const int gi_ = irow / gr;
               const float dri_ = ((float)(irow - gi_ * gr) + 0.5f - 0.5f * (float)gr) * dr32;
               const float ri_ = (float)(B.r_lo + (gi_ * gr + 0.5 * gr) * sh.dr64) + dri_;
-              float sv[5];
+              float sv[5], fsc = 1.f;
               double dist[5];
 #pragma unroll 1
               for (int k = 0; k < 5; ++k) {
                 const int l = m - 2 + k;
                 float d2;
-                const bool in = classify(gi_, ri_, dri_, irow, l, &d2);
+                const bool in = classify(gi_, ri_, dri_, irow, l, &d2, k == 2 ? &fsc : nullptr);
                 sv[k] = in ? __int_as_float(__float_as_int(d2) | 0x80000000) : d2;
                 dist[k] = (!B.periodic && (l < 0 || l >= NTH)) ? __longlong_as_double(0x7ff0000000000000LL)
                                                                : ray_distance64<NL>(sh, B, irow, wrapl(l));
               }
               if (signbit(sv[2])) {
                 float Id, Ir, Iu;
-                const float I = sh.half ? brightness_der(-sv[2], &Id, &Ir, &Iu, std::true_type{})
-                                        : brightness_der(-sv[2], &Id, &Ir, &Iu, std::false_type{});
+                float I = sh.generic ? brightness_der(-sv[2], &Id, &Ir, &Iu, std::true_type{})
+                                     : brightness_der(-sv[2], &Id, &Ir, &Iu, std::false_type{});
+                // a spot scales the point's brightness and its derivatives
+                I *= fsc; Id *= fsc; Ir *= fsc; Iu *= fsc;
                 const float W = boundary_weight(m, sv, m, irow, dist);
                 float v[12];
 #pragma unroll
@@ -2232,6 +2361,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             float dh;
             unsigned win = classify(gi, ri, dri, ii, c0 - 1, &dh) ? 1u : 0u;
             AnchorF ar;  // the current group's anchor, A_j and angle
+            int aiD = 0;  // its index
             float4 A01 = make_float4(0.f, 0.f, 0.f, 0.f);
             float2 cs = make_float2(1.f, 0.f);
             int gbase = 0;
@@ -2269,13 +2399,16 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             // gradient; an undecided ray waits for the block end
             auto colD = [&](int l, const cf t, bool& unc, auto hc) {
               cf dz, dw;
-              const float d2 = ray_eval(ar, t.x, t.y, ri, dri, nullptr, &dz, &dw);
+              float eb = 0.f;
+              const float d2 = ray_eval(ar, t.x, t.y, ri, dri, decltype(hc)::value ? &eb : nullptr, &dz, &dw);
               const bool in = d2 < ar.lo2;
               const bool u_ = !(in || d2 > ar.hi2);
               unc = unc || u_;
               win = (win << 1) | (in ? 1u : 0u);
               if (!u_) {
-                const float a = seed_of(in, d2, pg, rowacc, hc);
+                float fs = 1.f;
+                if constexpr (decltype(hc)::value) fs = in ? spot_factor(aiD, dw, eb, ii, l) : 1.f;
+                const float a = seed_of(in, d2, pg, rowacc, hc, fs);
                 if (a != 0.f) grad_core(dz, dw, t.x, t.y, ri, (float)l + 0.5f, A01, cs, a, pg);
               }
             };
@@ -2291,8 +2424,9 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                     if (d2 < ar.lo2 || d2 > ar.hi2) continue;
                     const bool in = decide(d2, eb, ii, l0 + k);
                     if (in) win |= 1u << (nb - 1 - k);
-                    const float a = sh.half ? seed_of(in, d2, pg, rowacc, std::true_type{})
-                                            : seed_of(in, d2, pg, rowacc, std::false_type{});
+                    const float fs = in ? spot_factor(aiD, dw, eb, ii, l0 + k) : 1.f;
+                    const float a = sh.generic ? seed_of(in, d2, pg, rowacc, std::true_type{}, fs)
+                                               : seed_of(in, d2, pg, rowacc, std::false_type{}, fs);
                     if (a != 0.f) grad_core(dz, dw, t.x, t.y, ri, (float)(l0 + k) + 0.5f, A01, cs, a, pg);
                   }
                   bm = centres(nb, first);
@@ -2305,6 +2439,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             while (l < c1) {
               const int mgrp = (int)__umulhi((unsigned int)l, gmagic);
               const int ai = gi * mth + mgrp;
+              aiD = ai;
               ar = anf[ai];
               A01 = ds.aA[ai];
               cs = ds.acs[ai];
@@ -2313,7 +2448,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               while (l < lend) {
                 const int nb = min(KB, lend - l);
                 bool unc = false;
-                if (sh.half) {
+                if (sh.generic) {
 #pragma unroll 1
                   for (int k = 0; k < nb; ++k) colD(l + k, tab_at(l + k - gbase), unc, std::true_type{});
                 } else {
@@ -2363,7 +2498,11 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     if (tid == 0) {
       double tot = 0.0;
       for (int w = 0; w < NW; ++w) tot += sh.red[w];
-      double A = tot / (sh.rho * sh.rho);
+      // unspotted normalisation A0 = S / rho^2; a spot divides by the
+      // unlensed flux 1 - c F_spot (N = spot_norm); an invalid spot gives NaN
+      const double A0 = tot / (sh.rho * sh.rho);
+      double A = A0 * sh.spot_norm;
+      if (sh.spot_bad) A = __longlong_as_double(0x7ff8000000000000LL);
       if (!(A == A) || isinf(A)) sh.status |= ICRS_ST_NAN;
       size_t o = (size_t)s * E + e;
       if (DER) {
@@ -2383,7 +2522,10 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         const double ir2 = 1.0 / (sh.rho * sh.rho);
         double dA[NPAR];
         for (int q = 0; q < NPAR; ++q) dA[q] = dS[q] * ir2;
-        dA[6] -= 2.0 * A / sh.rho;
+        dA[6] -= 2.0 * A0 / sh.rho;
+        // the spot's normalisation: dA = N dA0 + A0 dN, dN/du1 = N^2 c dF/du1
+        for (int q = 0; q < NPAR; ++q) dA[q] *= sh.spot_norm;
+        dA[7] += A * sh.spot_gu;
         bool bad = false;
         for (int q = 0; q < NPAR; ++q) bad |= !(dA[q] == dA[q]) || isinf(dA[q]);
         if (bad) sh.status |= ICRS_ST_NAN;
@@ -2512,7 +2654,7 @@ static size_t mag_smem_bytes(int NL, const icrs_grid& g, int pmax, int has_plo, 
   b += sizeof(cf) * NP + 4 * sizeof(float) * NP;
   b += sizeof(short) * ((NP + 7) & ~(size_t)7);
   b += 3 * ((NP + 15) & ~(size_t)15);
-  b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + 16 + sizeof(AnchorF) * MAXANCH;
+  b += 2 * sizeof(double) * pmax + sizeof(int) * QMAX + 16 + (sizeof(AnchorF) + sizeof(float2)) * MAXANCH;
   const int NW = nt / 32;
   (void)defer;
   b += sizeof(int) * NW * 2 * dq_entries(NL);  // per-warp boundary queues

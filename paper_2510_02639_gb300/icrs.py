@@ -46,7 +46,9 @@ class IcrsParams(ctypes.Structure):
                 ("s", ctypes.c_double), ("q", ctypes.c_double),
                 ("q2", ctypes.c_double), ("q3", ctypes.c_double), ("s2", ctypes.c_double),
                 ("s3", ctypes.c_double), ("psi", ctypes.c_double), ("u2", ctypes.c_double),
-                ("a1", ctypes.c_double), ("a2", ctypes.c_double), ("a3", ctypes.c_double), ("a4", ctypes.c_double)]
+                ("a1", ctypes.c_double), ("a2", ctypes.c_double), ("a3", ctypes.c_double), ("a4", ctypes.c_double),
+                ("spot_x", ctypes.c_double), ("spot_y", ctypes.c_double), ("spot_r", ctypes.c_double),
+                ("spot_c", ctypes.c_double)]
 
 
 class IcrsGrid(ctypes.Structure):
@@ -61,7 +63,8 @@ PARAMS_DTYPE = np.dtype([("t0", "<f8"), ("tE", "<f8"), ("u0", "<f8"), ("alpha", 
                          ("rho", "<f8"), ("u1", "<f8"), ("n_lens", "<i4"), ("reserved", "<i4"),
                          ("s", "<f8"), ("q", "<f8"), ("q2", "<f8"), ("q3", "<f8"),
                          ("s2", "<f8"), ("s3", "<f8"), ("psi", "<f8"), ("u2", "<f8"),
-                         ("a1", "<f8"), ("a2", "<f8"), ("a3", "<f8"), ("a4", "<f8")])
+                         ("a1", "<f8"), ("a2", "<f8"), ("a3", "<f8"), ("a4", "<f8"),
+                         ("spot_x", "<f8"), ("spot_y", "<f8"), ("spot_r", "<f8"), ("spot_c", "<f8")])
 assert PARAMS_DTYPE.itemsize == ctypes.sizeof(IcrsParams)
 
 

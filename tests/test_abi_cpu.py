@@ -52,7 +52,7 @@ def test_struct_layouts(libmod, tmp_path):
         assert got[(st, "size")] == ctypes.sizeof(cls), st
         for f, _ in cls._fields_:
             assert got[(st, f)] == getattr(cls, f).offset, (st, f)
-    assert ctypes.sizeof(libmod.IcrsParams) == libmod.PARAMS_DTYPE.itemsize == 19 * 8
+    assert ctypes.sizeof(libmod.IcrsParams) == libmod.PARAMS_DTYPE.itemsize == 23 * 8
     g = libmod.make_grid()
     assert (g.n_r, g.n_theta, g.n_limb, g.n_bins_r, g.n_bins_theta) == (64, 256, 500, 32, 128)
     assert abs(g.delta_c - 0.02) < 1e-15 and abs(g.margin - 0.05) < 1e-15

@@ -232,6 +232,22 @@ def test_dA_power_series_profile(G, oracle_mod):
     assert_dA(dA, dAo, "power-series law", Ao)
 
 
+def test_dA_spotted_source(G, oracle_mod):
+    """A spotted source (centre (0.3, -0.2), radius 0.4, contrast 0.7; the
+    spot's edge is a discrete decision, so its motion does not enter the
+    almost-everywhere derivative, and the unlensed flux 1 - c F_spot depends
+    on u1): dA/dp of the adjoint against the oracle's FP64 forward mode on 12
+    epochs of the caustic-crossing curve."""
+    params, t = I.caustic_crossing_binary()
+    params = [dict(params[0], spot_x=0.3, spot_y=-0.2, spot_r=0.4, spot_c=0.7)]
+    t = t[:, ::42]
+    g = I.grid()
+    A, dA, st, grad = gpu_dA(G, params, t, g)
+    Ao, dAo, so = oracle_mod.magnification_fwd(params, t, g)
+    assert np.all(np.abs(A / Ao - 1.0) <= TAU)
+    assert_dA(dA, dAo, "spotted source", Ao)
+
+
 def test_paper_gradient_rules(G, oracle_mod):
     """The paper's gradient rules (grid grad_rule = 1, s_fac = 100: sigmoid
     indicator derivative, fixed f'(delta) = 2/3) in the adjoint against the

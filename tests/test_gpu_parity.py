@@ -272,6 +272,34 @@ def test_power_series_profiles(G, oracle_mod, coef):
             assert_status(st, so, what=f"a={coef} split={split}")
 
 
+@pytest.mark.parametrize("spot", [(0.3, -0.2, 0.4, 0.7), (-0.5, 0.1, 0.3, 0.5), (0.0, 0.0, 1.0, 0.6)])
+def test_spotted_sources(G, oracle_mod, spot):
+    """A circular spot (centre, radius in rho, contrast) on a linearly
+    limb-darkened source, on the caustic-crossing curve and on 64 batch
+    epochs (one with a power-series law too): against the oracle at 1e-5
+    with the same status bits; a spot outside the disk gives NaN and
+    ICRS_ST_NAN on both sides."""
+    sx, sy, sr, sc = spot
+    sp = dict(spot_x=sx, spot_y=sy, spot_r=sr, spot_c=sc)
+    base, t = I.caustic_crossing_binary(n_epochs=40)
+    bp, bt = I.binary_batch()
+    sel = [(s_, e) for s_ in range(0, 64, 8) for e in range(0, 10000, 1250)]
+    cases = [([dict(base[0], **sp)], t),
+             ([dict(bp[s_], **sp) for s_, _ in sel], np.array([[bt[s_, e]] for s_, e in sel])),
+             ([dict(base[0], a1=0.3, a3=-0.1, **sp)], t[:, ::4])]
+    g = I.grid()
+    for params, tt in cases:
+        A, st = run_gpu(G, params, tt, g)
+        Ao, so = oracle_mod.magnification(params, tt, g)
+        assert_parity(A, Ao, what=f"spot {spot}")
+        assert_status(st, so, what=f"spot {spot}")
+    bad = [dict(base[0], spot_x=0.8, spot_y=0.0, spot_r=0.3, spot_c=0.5)]
+    A, st = run_gpu(G, bad, t[:, :3], g)
+    Ao, so = oracle_mod.magnification(bad, t[:, :3], g)
+    assert np.all(np.isnan(A)) and np.all(np.isnan(Ao))
+    assert np.all(st & 16) and np.all(so & 16)
+
+
 def test_qualification_sample_at_headline_grid(G):
     """The 512-epoch qualification sample of the batch (peak epochs, random
     epochs, small sources at moderate magnification, sources inside a
