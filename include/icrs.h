@@ -51,6 +51,8 @@ extern "C" {
 #define ICRS_ST_OVERFLOW 32u /* an on-chip table overflowed; a decision was taken in FP32 */
 #define ICRS_ST_LIMB 64u     /* surrogate features: the image count changes across the source disk */
 #define ICRS_ST_ROUGH 128u   /* surrogate features: the limb magnification varies on the source's scale */
+#define ICRS_ST_SPOT (1u << 16)    /* surrogate features: the source has a spot (not radially symmetric) */
+#define ICRS_ST_PROFILE (1u << 17) /* surrogate features: the law has u2 or a1..a4, which no network input carries */
 /* Threshold of ICRS_ST_ROUGH: the angular harmonics of order >= 3 of A_ps
  * along the 32 limb points, summed in magnitude over both signs of the order,
  * relative to A_ps at the centre. */
@@ -327,7 +329,10 @@ int icrs_magnification_indexed(const icrs_params* p, int S, const double* t, int
  *             point-source images at the source centre and at the 32 limb
  *             points w_c + rho e^{i pi k / 16}.  The network reads the first 7.
  *             b = 1e4 log(1 + f_u (mean_k A_ps(limb k) / A_ps - 1)), with
- *             f_u = (15 - 7 u1) / (10 (3 - u1)), is the second-order
+ *             f_u = <r^2> / rho^2 the second moment of the source's
+ *             brightness ((15 - 7 u1) / (10 (3 - u1)) for the linear law,
+ *             1/2 on a uniform grid; the quadratic and power-series terms
+ *             u2, a1..a4 enter by their moments), is the second-order
  *             finite-source estimate: the network predicts y - b
  */
 #define ICRS_MLP_NPARAM 50818
@@ -398,7 +403,12 @@ int icrs_mlp_train_step_noalloc(float* theta, float* adam_m, float* adam_v, void
  *             H = (1/32) sum_{m=3..29} |sum_k (A_k - A_c) e^{-2 pi i m k / 32}| / A_c
  *             over the limb magnifications A_k at w_c + rho e^{2 pi i k / 32}:
  *             structure on the scale of the source (a caustic a few rho
- *             away) that the second-order estimate of feature 7 misses
+ *             away) that the second-order estimate of feature 7 misses;
+ *             plus ICRS_ST_SPOT when spot_c != 0 and spot_r > 0 (the
+ *             estimate assumes a radially symmetric source) and, unless
+ *             g->uniform, ICRS_ST_PROFILE when u2 or one of a1..a4 is nonzero
+ *             (the network was given u1 only; the estimate itself uses the
+ *             law's second moment and stays valid)
  */
 int icrs_surrogate_features(const icrs_params* p, int S, const double* t, int E,
                             const icrs_grid* g, float* features, double* A_ps,
@@ -429,7 +439,7 @@ size_t icrs_surrogate_gate_workspace_bytes(int n);
 /*
  * Error gate.  Epoch i is accepted when all of these hold:
  *   - its feature status is 0 (clean solves, the same image count across
- *     the disk, and no ICRS_ST_ROUGH);
+ *     the disk, no ICRS_ST_ROUGH, no spot and no law beyond u1);
  *   - features[i][6] >= caustic_min;
  *   - exp(s_i / 2) <= sigma_max;
  *   - |mu_i| <= mu_max and |features[i][7]| <= b_max;
@@ -454,7 +464,8 @@ int icrs_surrogate_gate(const float* pred, const float* features, const double* 
  * 3.4 (iii) runs the extended-source computation only on a preselected set
  * of epochs near caustics.  Epoch e of light curve s (item q = s * E + e of
  * an [S][E] problem) is near a caustic unless all of these hold:
- *   - its feature status is 0 (as in icrs_surrogate_gate);
+ *   - its feature status is 0 apart from ICRS_ST_PROFILE (the second-order
+ *     estimate holds for every radial law);
  *   - features[q][6] >= caustic_min;
  *   - |features[q][7]| <= b_max (the second-order estimate b);
  *   - A_ps[q] <= A_max, or <= A_small when rho < rho_min.

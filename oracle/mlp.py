@@ -210,6 +210,8 @@ def adam(theta, m, v, grad, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 ST_LIMB = 64  # the image count changes between the source centre and a limb point
 ST_ROUGH = 128  # the limb magnification varies on the scale of the source (limb_roughness > ROUGH_MAX)
+ST_SPOT = 1 << 16  # the source carries a spot: its brightness is not radially symmetric
+ST_PROFILE = 1 << 17  # the law has terms beyond the linear one (u2, a1..a4), which no network input carries
 ROUGH_MAX = 1e-3
 
 
@@ -224,6 +226,25 @@ def limb_roughness(A_c, A_limb):
     return np.sum(np.abs(c[:, 3:30]), axis=1) / 32.0 / A_c
 
 
+def profile_r2(p: dict) -> float:
+    """<r^2> / rho^2 of the source's brightness over its disk, for the
+    law the oracle integrates (Appendix A.2's linear law plus the quadratic
+    and mu^(k/2) terms that stand for the abstract's arbitrary profiles):
+    with mu = sqrt(1 - x), x = r^2 / rho^2, the law is a sum of powers
+    c_p mu^p (c_0 = 1 - u1 - u2 - sum a_k, c_1 = u1 + 2 u2, c_2 = -u2, and
+    a_k at p = k / 2), and over the disk (dA = pi rho^2 dx)
+        int_0^1 mu^p dx = 2 / (p + 2),   int_0^1 mu^p x dx = 2 / (p + 2) - 2 / (p + 4),
+    so <r^2> / rho^2 = sum c_p (2/(p+2) - 2/(p+4)) / sum c_p 2/(p+2).  The
+    linear law gives (15 - 7 u) / (10 (3 - u))."""
+    u1, u2 = p["u1"], p.get("u2", 0.0)
+    a = [p.get("a%d" % k, 0.0) for k in range(1, 5)]
+    terms = [(0.0, 1.0 - u1 - u2 - sum(a)), (1.0, u1 + 2.0 * u2), (2.0, -u2)]
+    terms += [(k / 2.0, a[k - 1]) for k in range(1, 5)]
+    m0 = sum(c * 2.0 / (q + 2.0) for q, c in terms)
+    m1 = sum(c * (2.0 / (q + 2.0) - 2.0 / (q + 4.0)) for q, c in terms)
+    return m1 / m0
+
+
 def features(p: dict, t, grid: dict, return_roughness: bool = False):
     """Surrogate features of one parameter set at times t, from the oracle's
     point-source images at the source centre and at the 32 limb points
@@ -232,7 +253,9 @@ def features(p: dict, t, grid: dict, return_roughness: bool = False):
     Feature 6 is log10 of the smallest |det J| over all those images, with
     det J = 1 - |sum_i eps_i / (z - a_i)^2|^2 (Eq. detJ), clamped to [-6, 1];
     status gains ST_LIMB when a limb point's image count differs from the
-    centre's, and ST_ROUGH when H > ROUGH_MAX or H is not finite."""
+    centre's, ST_ROUGH when H > ROUGH_MAX or H is not finite, ST_SPOT for a
+    spotted source (spot_c != 0 and spot_r > 0, dark or bright) and, unless
+    the grid is uniform, ST_PROFILE for a law with u2 or a1..a4 nonzero."""
     import oracle
     w = oracle.source_centre(p, t)
     A, nimg, z, st = oracle.point_source(p, grid, w)
@@ -258,11 +281,16 @@ def features(p: dict, t, grid: dict, return_roughness: bool = False):
             if nl[i] != nimg[i] or sl[i]:
                 st[i] |= np.uint32(ST_LIMB)
     # second-order estimate of the disk average: A + (<r^2>/4) lap A, with the
-    # limb mean minus the centre = (rho^2/4) lap A and, for the linear law
-    # I = 1 - u + u sqrt(1 - r^2/rho^2), <r^2>/rho^2 = (15 - 7u) / (10 (3 - u))
-    u = p["u1"]
-    fu = (15.0 - 7.0 * u) / (10.0 * (3.0 - u))
+    # limb mean minus the centre = (rho^2/4) lap A and <r^2> the brightness's
+    # second moment (profile_r2; 1/2 for the uniform disk of a uniform grid,
+    # whose brightness carries no law)
+    uniform = bool(grid.get("uniform", 0))
+    fu = 0.5 if uniform else profile_r2(p)
     base = 1e4 * np.log1p(fu * (Alimb / A - 1.0))
+    if p.get("spot_c", 0.0) != 0.0 and p.get("spot_r", 0.0) > 0.0:
+        st |= np.uint32(ST_SPOT)
+    if not uniform and (p.get("u2", 0.0) != 0.0 or any(p.get("a%d" % k, 0.0) != 0.0 for k in range(1, 5))):
+        st |= np.uint32(ST_PROFILE)
     with np.errstate(divide="ignore", invalid="ignore"):
         rough = limb_roughness(A, Ak)
     st[~(rough <= ROUGH_MAX)] |= np.uint32(ST_ROUGH)

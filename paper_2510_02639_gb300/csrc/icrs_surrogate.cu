@@ -459,6 +459,24 @@ __global__ void reduce_adam_kernel(float* __restrict__ theta, float* __restrict_
 
 // ---------------------------------------------------------------- features
 constexpr float TARGET_SCALE = 1e4f;
+
+// <r^2> / rho^2 of the brightness over the source disk.  The law
+// I0 [1 - u1 (1 - mu) - u2 (1 - mu)^2 - sum_k a_k (1 - mu^(k/2))] is a sum of
+// powers c_p mu^p, mu = sqrt(1 - x), x = r^2 / rho^2, with c_0 = 1 - u1 - u2 -
+// sum a, c_1 = u1 + 2 u2, c_2 = -u2 and a_k at p = k/2; over the disk
+// int mu^p dx = 2/(p+2) and int mu^p x dx = 2/(p+2) - 2/(p+4).
+__device__ double profile_r2(const icrs_params& p) {
+  const double a[4] = {p.a1, p.a2, p.a3, p.a4};
+  const double c0 = 1.0 - p.u1 - p.u2 - (a[0] + a[1] + a[2] + a[3]);
+  double m0 = c0 + p.u1 * (2.0 / 3.0) + p.u2 * (2.0 * (2.0 / 3.0) - 0.5);
+  double m1 = c0 * 0.5 + (p.u1 + 2.0 * p.u2) * (2.0 / 3.0 - 0.4) - p.u2 * (0.5 - 1.0 / 3.0);
+  for (int k = 1; k <= 4; ++k) {
+    const double q = 0.5 * k;
+    m0 += a[k - 1] * (2.0 / (q + 2.0));
+    m1 += a[k - 1] * (2.0 / (q + 2.0) - 2.0 / (q + 4.0));
+  }
+  return m1 / m0;
+}
 constexpr int NLIMB_SG = 32;  // source-limb points of the feature kernel
 constexpr int FEAT_THREADS = 128;  // threads (epochs) per feature block
 static_assert((NLIMB_SG & (NLIMB_SG - 1)) == 0, "the harmonic index wraps with a mask");
@@ -516,10 +534,12 @@ __global__ void features_kernel(const icrs_params* __restrict__ P, int S, const 
   if (!(rough <= ICRS_ROUGH_MAX)) stf |= ICRS_ST_ROUGH;
   // second-order finite-source estimate: the limb mean minus the centre is
   // (rho^2 / 4) lap A to leading order, and the disk average of A is
-  // A + (<r^2> / 4) lap A with <r^2> / rho^2 = (15 - 7 u) / (10 (3 - u)) for
-  // the linear law (1/2 for a uniform disk)
-  const double fu = (15.0 - 7.0 * prm.u1) / (10.0 * (3.0 - prm.u1));
+  // A + (<r^2> / 4) lap A, <r^2> the brightness's second moment
+  const double fu = g.uniform ? 0.5 : profile_r2(prm);
   const double est = ps.A > 0.0 ? TARGET_SCALE * log1p(fu * (Alimb / ps.A - 1.0)) : 0.0;
+  if (prm.spot_c != 0.0 && prm.spot_r > 0.0) stf |= ICRS_ST_SPOT;
+  if (!g.uniform && (prm.u2 != 0.0 || prm.a1 != 0.0 || prm.a2 != 0.0 || prm.a3 != 0.0 || prm.a4 != 0.0))
+    stf |= ICRS_ST_PROFILE;
   float* f = feat + idx * 8;
   f[0] = (float)w.x;
   f[1] = (float)w.y;
@@ -624,7 +644,9 @@ __global__ void epoch_near_kernel(const float* __restrict__ feat, const double* 
   const int q = blockIdx.x * GB + threadIdx.x;
   if (q >= n) return;
   const float base = feat[(size_t)q * 8 + 7];
-  const bool ok = st_ps[q] == 0u && feat[(size_t)q * 8 + 6] >= caustic_min && fabsf(base) <= b_max &&
+  // the estimate holds for any radial law, so ICRS_ST_PROFILE does not route here
+  const bool ok = (st_ps[q] & ~ICRS_ST_PROFILE) == 0u && feat[(size_t)q * 8 + 6] >= caustic_min &&
+                  fabsf(base) <= b_max &&
                   A_ps[q] <= (feat[(size_t)q * 8 + 4] >= log10f(rho_min) + 3.0f ? A_max : A_small);
   near[q] = ok ? 0 : 1;
 }

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libicrs.so")
 
 ICRS_OK, ICRS_EINVAL, ICRS_ECUDA, ICRS_ETIMEOUT, ICRS_EUNSUPPORTED = 0, 1, 2, 3, 4
 ST_NONCONV, ST_IMGCOUNT, ST_SECTCAP, ST_EDGE, ST_NAN, ST_OVERFLOW, ST_LIMB, ST_ROUGH = 1, 2, 4, 8, 16, 32, 64, 128
+ST_SPOT, ST_PROFILE = 1 << 16, 1 << 17
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTED = ("icrs_grid_default", "icrs_point_source", "icrs_magnification",

@@ -91,7 +91,9 @@ def test_product_path_has_no_oracle_import():
 
 def header_defines():
     src = open(os.path.join(ROOT, "include", "icrs.h")).read()
-    return {k: v for k, v in re.findall(r"#define\s+(ICRS_[A-Z0-9_]+)\s+([0-9.eE+-]+)u?\b", src)}
+    d = {k: v for k, v in re.findall(r"#define\s+(ICRS_[A-Z0-9_]+)\s+([0-9.eE+-]+)u?\b", src)}
+    d.update({k: str(1 << int(n)) for k, n in re.findall(r"#define\s+(ICRS_[A-Z0-9_]+)\s+\(1u << (\d+)\)", src)})
+    return d
 
 
 def test_status_bits_and_constants_agree(libmod):
@@ -99,9 +101,10 @@ def test_status_bits_and_constants_agree(libmod):
     threshold carry the header's values (each side defines its own)."""
     from oracle import mlp as M
     d = header_defines()
-    for name in ("NONCONV", "IMGCOUNT", "SECTCAP", "EDGE", "NAN", "OVERFLOW", "LIMB", "ROUGH"):
+    for name in ("NONCONV", "IMGCOUNT", "SECTCAP", "EDGE", "NAN", "OVERFLOW", "LIMB", "ROUGH", "SPOT", "PROFILE"):
         assert int(d["ICRS_ST_" + name]) == getattr(libmod, "ST_" + name), name
     assert int(d["ICRS_ST_LIMB"]) == M.ST_LIMB and int(d["ICRS_ST_ROUGH"]) == M.ST_ROUGH
+    assert int(d["ICRS_ST_SPOT"]) == M.ST_SPOT and int(d["ICRS_ST_PROFILE"]) == M.ST_PROFILE
     assert float(d["ICRS_ROUGH_MAX"]) == M.ROUGH_MAX
     assert int(d["ICRS_MLP_NPARAM"]) == libmod.MLP_NPARAM == M.N_PARAMS
     assert int(d["ICRS_MLP_PACK_BYTES"]) == libmod.MLP_PACK_BYTES

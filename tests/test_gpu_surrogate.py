@@ -154,6 +154,47 @@ def test_features_match_oracle(G, oracle_mod):
         np.testing.assert_array_equal((st.cpu().numpy().reshape(3, 200)[s] & 128)[far], (so & 128)[far])
 
 
+def test_features_profiles_and_spots(G, oracle_mod):
+    """Quadratic and power-series laws and a dark or bright spot: feature 7
+    (the second-order estimate with the law's own second moment) and the
+    ICRS_ST_SPOT / ICRS_ST_PROFILE bits equal the oracle's; the learned gate
+    routes both kinds of set whatever the network predicts, the non-learned
+    gate routes the spotted sets and treats the other laws like the linear one."""
+    import torch
+    from oracle import mlp as M
+    params, t = I.binary_batch(n_sets=5, n_epochs=120, seed=37)
+    extra = [dict(u2=0.2), dict(a1=0.5, a3=-0.2), dict(spot_x=0.2, spot_y=-0.1, spot_r=0.3, spot_c=0.6),
+             dict(spot_x=0.0, spot_y=0.4, spot_r=0.2, spot_c=-0.5), {}]
+    params = [dict(p, **x) for p, x in zip(params, extra)]
+    S, E = t.shape
+    g = I.grid()
+    pd = G.params_to_device(params)
+    tt = torch.tensor(t, device="cuda")
+    feat, Aps, st = G.surrogate_features(pd, tt, G.grid_from_dict(g, 2))
+    f_ = feat.cpu().numpy().reshape(S, E, 8); s_ = st.cpu().numpy().reshape(S, E)
+    for s in range(S):
+        fo, Ao, so, Ho = M.features(params[s], t[s], g, return_roughness=True)
+        np.testing.assert_allclose(f_[s][:, 7], fo[:, 7], rtol=1e-5, atol=1e-3)
+        np.testing.assert_array_equal(s_[s] & (M.ST_SPOT | M.ST_PROFILE), so & (M.ST_SPOT | M.ST_PROFILE))
+    want = [M.ST_PROFILE, M.ST_PROFILE, M.ST_SPOT, M.ST_SPOT, 0]
+    for s in range(S):
+        assert np.all(s_[s] & (M.ST_SPOT | M.ST_PROFILE) == want[s]), s
+    n = S * E
+    pred = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+    pred[:, 1] = -20.0  # confident, zero correction: only the status and feature rules decide
+    _, idx, nr = G.surrogate_gate(pred, feat, Aps, st, sigma_max=1.0, mu_max=1e9, b_max=1e9, caustic_min=-7.0)
+    routed = np.zeros(n, bool); routed[idx.cpu().numpy()[: int(nr.item())]] = True
+    routed = routed.reshape(S, E)
+    assert routed[:4].all()
+    np.testing.assert_array_equal(routed[4], (s_[4] != 0))
+    _, idx, nr = G.epoch_gate(feat, Aps, st, S, E, 0, 1, 1e9, -7.0)
+    routed = np.zeros(n, bool); routed[idx.cpu().numpy()[: int(nr.item())]] = True
+    routed = routed.reshape(S, E)
+    assert routed[2:4].all()
+    for s in (0, 1, 4):
+        np.testing.assert_array_equal(routed[s], (s_[s] & ~np.uint32(M.ST_PROFILE)) != 0)
+
+
 def test_roughness_bit_across_a_caustic_approach(G, oracle_mod):
     """A source passing within a few rho of a planetary caustic (rho = 7.5e-3,
     q = 3.2e-4, s = 1.56): the limb harmonics rise from ~1e-4 to ~1 of A_ps and

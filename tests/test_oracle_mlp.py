@@ -98,6 +98,70 @@ def test_ld_second_moment_closed_form():
         assert abs(num / den - (15 - 7 * u) / (10 * (3 - u))) < 1e-10
 
 
+PROFILE_SETS = [  # (u1, u2, (a1, a2, a3, a4))
+    (0.0, 0.0, (0.0, 0.0, 0.0, 0.0)),
+    (0.4, 0.25, (0.0, 0.0, 0.0, 0.0)),
+    (0.0, 0.0, (0.6, 0.3, -0.2, 0.1)),
+    (0.3, 0.1, (0.2, 0.0, 0.15, 0.0)),
+]
+
+
+def test_profile_second_moment_quadrature():
+    """<r^2>/rho^2 of profile_r2 against quadrature of the law written out,
+    I = 1 - u1 (1 - mu) - u2 (1 - mu)^2 - sum_k a_k (1 - mu^(k/2)) with
+    mu = sqrt(1 - r^2) (the normalisation cancels), and the linear law's
+    closed form.  A dropped term, a wrong power or a sign error in any
+    coefficient moves the ratio by far more than the tolerance."""
+    from scipy.integrate import quad
+    for u1, u2, a in PROFILE_SETS:
+        def I(r):
+            mu = np.sqrt(max(0.0, 1.0 - r * r))
+            return (1.0 - u1 * (1.0 - mu) - u2 * (1.0 - mu) ** 2
+                    - sum(a[k - 1] * (1.0 - mu ** (k / 2.0)) for k in range(1, 5)))
+        num = quad(lambda r: I(r) * r ** 3, 0, 1, epsabs=1e-14, limit=200)[0]
+        den = quad(lambda r: I(r) * r, 0, 1, epsabs=1e-14, limit=200)[0]
+        p = {"u1": u1, "u2": u2, **{"a%d" % k: a[k - 1] for k in range(1, 5)}}
+        assert abs(M.profile_r2(p) - num / den) < 1e-9, (u1, u2, a)
+    for u in (0.0, 0.55):
+        assert abs(M.profile_r2({"u1": u}) - (15 - 7 * u) / (10 * (3 - u))) < 1e-14
+    assert abs(M.profile_r2({"u1": 0.0}) - 0.5) < 1e-15  # uniform disk: <r^2> = rho^2 / 2
+
+
+def test_second_order_estimate_single_lens_profiles(oracle_mod):
+    """Far single lens, power-series and quadratic laws: the second-order
+    estimate with the law's own second moment reproduces the closed-form
+    disk magnification of that law to O((rho/u)^4), and the feature status
+    carries ST_PROFILE (no network input holds u2 or a1..a4) but no other bit."""
+    from tests import closed_forms as CF
+    from paper_2510_02639_gb300 import inputs as I
+    rho, u_over_rho = 0.01, 10.0
+    u = u_over_rho * rho
+    for u1, u2, a in PROFILE_SETS[1:]:
+        p = I.binary(q=1e-9, s=50.0, rho=rho, u1=u1, u0=u, t0=0.0, tE=1.0, alpha=0.0)
+        p.update(u2=u2, **{"a%d" % k: a[k - 1] for k in range(1, 5)})
+        f, Aps, st = M.features(p, [0.0], I.grid())
+        exact = CF.single_lens_profile_disk(u, rho, u1, u2, a, n_v=64, n_limb=2000)
+        est = Aps[0] * np.exp(f[0, 7] * 1e-4)
+        assert abs(est / exact - 1.0) < 3.0 * (rho / u) ** 4, (u1, u2, a, est, exact)
+        assert abs(Aps[0] / exact - 1.0) > 10 * abs(est / exact - 1.0)
+        assert int(st[0]) == M.ST_PROFILE
+
+
+def test_feature_status_spot(oracle_mod):
+    """A spotted source sets ST_SPOT (the estimate assumes a radially
+    symmetric source), dark or bright and on a uniform grid too; a zero
+    contrast or a zero radius is no spot.  A uniform grid ignores the law's
+    terms beyond u1, so it sets no ST_PROFILE."""
+    from paper_2510_02639_gb300 import inputs as I
+    base = I.binary(q=1e-9, s=50.0, rho=0.01, u1=0.5, u0=0.1, t0=0.0, tE=1.0, alpha=0.0)
+    for sp, want in (((0.3, 0.1, 0.4, 0.5), M.ST_SPOT), ((0.3, 0.1, 0.4, -0.5), M.ST_SPOT),
+                     ((0.3, 0.1, 0.4, 0.0), 0), ((0.3, 0.1, 0.0, 0.5), 0)):
+        p = dict(base, spot_x=sp[0], spot_y=sp[1], spot_r=sp[2], spot_c=sp[3])
+        for uniform in (0, 1):
+            _, _, st = M.features(dict(p, u2=0.2), [0.0], dict(I.grid(), uniform=uniform))
+            assert int(st[0]) == want | (0 if uniform else M.ST_PROFILE), (sp, uniform, int(st[0]))
+
+
 def test_second_order_estimate_single_lens(oracle_mod):
     """Far single lens (q = 1e-9, s = 50): the second-order finite-source
     estimate b from the 32 limb point-source magnifications reproduces the
