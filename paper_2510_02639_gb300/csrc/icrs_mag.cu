@@ -459,6 +459,17 @@ __device__ __forceinline__ T fdelta_prime(T d, T delta_c, int uniform) {
 }
 
 // ---------------------------------------------------------------- kernel
+// A set whose law has half-integer powers of mu (a1 or a3, on a limb-darkened
+// grid) or a spot: the binary forward launch gives these sets to the kernel's
+// generic instantiation and all others to the linear one, which carries none
+// of their code.
+__device__ inline bool generic_law(const icrs_params& p, const icrs_grid& g) {
+  return p.spot_c != 0.0 || (!g.uniform && (p.a1 != 0.0 || p.a3 != 0.0));
+}
+
+// LAW = 0: only the sets without a generic law (their code compiled out);
+// LAW = 1: only the sets with one; LAW = 2: every set, the law decided at run
+// time.
 // DER = true: also the derivative of A with respect to (t0, tE, u0, alpha, s,
 // q, rho, u1) (binary lens): reverse mode over the rays (adjoint seeds per
 // ray, then each seeded ray's gradient), forward mode (8 tangents) over the
@@ -472,7 +483,7 @@ struct DerOut {
   double* chi2;        // [S] accumulated, or NULL
 };
 
-template <int NL, bool DER, int NTB>
+template <int NL, bool DER, int NTB, int LAW>
 __global__ void __launch_bounds__(NTB, 1)
 mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ T_, int E,
            icrs_grid g, int tiles_per_block, double* __restrict__ A_out, uint32_t* __restrict__ st_out,
@@ -533,10 +544,17 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
   // tiles: all (set, epoch) pairs, or the listed indices s * E + e
   const long long ntiles = items ? (long long)n_items : (long long)S * E;
   const long long t_begin = (long long)blockIdx.x * tiles_per_block;
+  int law_set = -1;
+  bool law_gen = false;
   for (long long tile = t_begin; tile < t_begin + tiles_per_block && tile < ntiles; ++tile) {
     long long q = items ? (long long)items[tile] : tile;
     if (q < 0 || q >= (long long)S * E) continue;  // block-uniform: skips the whole tile
     const int s = (int)(q / E), e = (int)(q % E);
+    if constexpr (LAW != 2) {
+      // the other instantiation takes this set (block-uniform)
+      if (s != law_set) { law_set = s; law_gen = generic_law(P[s], g); }
+      if (law_gen != (LAW == 1)) continue;
+    }
     // ------------------------------------------------ set and epoch set-up
     if (tid == 0) {
       if (s != sh.cur_set) {
@@ -621,7 +639,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
     __syncthreads();
     const int ll = sh.L.ll;
     const float rho32 = (float)sh.rho;
-    if (sh.spot_new) {
+    if (LAW != 0 && sh.spot_new) {
       // the spot's share of the unspotted flux F_spot = int_spot I dA (rho
       // units, the disk's flux is 1) and dF_spot/du1, once per set: polar
       // quadrature about the spot centre, the periodic trapezoid rule in the
@@ -1523,7 +1541,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         cd zc = mk(rc * cs, rc * sn);
         cd wsd = lens_map<NL, double>(sh.L.eps, sh.L.a, zc) - sh.wc;
         const cf ws = tof(R * wsd);
-        if (sh.spot) spc[an] = make_float2((float)(sh.rho * (cs * sh.spot_x + sn * sh.spot_y)),
+        if (LAW != 0 && sh.spot) spc[an] = make_float2((float)(sh.rho * (cs * sh.spot_x + sn * sh.spot_y)),
                                            (float)(sh.rho * (cs * sh.spot_y - sn * sh.spot_x)));
         // error bound of |Delta w'|: anchor term plus rounding of the ray's
         // offset (at most the group half-diagonal) and of its image term
@@ -1627,7 +1645,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         const float x = fmaxf(fmaf(-d2, irho2, 1.0f), 1e-30f);
         const float mu = x * rsqrtf(x);
         float I = fmaf(c2f, x, fmaf(c1f, mu, c0f));
-        if (sh.half) I = fmaf(sqrtf(mu), fmaf(sh.c3h, mu, sh.c1h), I);
+        if (LAW != 0 && sh.half) I = fmaf(sqrtf(mu), fmaf(sh.c3h, mu, sh.c1h), I);
         return I;
       };
       // I and dI/dd, dI/drho, dI/du1 at squared distance d2:
@@ -1647,7 +1665,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         // k = (dI/dmu) / mu / rho^2
         float k = x > 0.f ? (c1f * rs + 2.0f * c2f) * irho2 : 0.f;
         if constexpr (decltype(hc)::value) {
-          if (sh.half && x > 0.f) {
+          if (LAW != 0 && sh.half && x > 0.f) {
             // s (c1h + c3h mu): dI/dmu = c1h / (2 s) + 1.5 c3h s, s = mu^(1/2)
             const float c1h = sh.c1h, c3h = sh.c3h;
             const float s_ = sqrtf(sx);
@@ -1892,7 +1910,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         const float spot_r2 = spot_rr * spot_rr;
         const float spot_f = (float)(1.0 - sh.spot_c);
         auto spot_factor = [&](int ai, const cf dw, float eb, int irow, int lw) -> float {
-          if (!sh.spot) return 1.f;
+          if (LAW == 0 || !sh.spot) return 1.f;
           const float2 c = spc[ai];
           const float ex = dw.x - c.x, ey = dw.y - c.y;
           const float q = fmaf(ex, ex, ey * ey);
@@ -1958,6 +1976,9 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
         };
         const float2 irho22 = make_float2(irho2, irho2), one2 = make_float2(1.0f, 1.0f);
         const float2 c1f2 = make_float2(c1f, c1f), c2f2 = make_float2(c2f, c2f);
+        // the half-power coefficients, read only by the generic instantiation
+        const float2 c1h2 = LAW == 1 ? make_float2(sh.c1h, sh.c1h) : one2;
+        const float2 c3h2 = LAW == 1 ? make_float2(sh.c3h, sh.c3h) : one2;
         // the queued points: one per lane, each re-evaluates its stencil
         // (rays m - 2 .. m + 2, signed squared distances, negative inside)
         auto flush_queue = [&]() {
@@ -2083,7 +2104,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                   if (d2 < lo2g || d2 > hi2g) continue;
                   if (decide(d2, eb, ii, l0 + k)) {
                     win |= 1u << (nb - 1 - k);
-                    add_in(true, sqrtf(fmaxf(__fmaf_rn(-d2, irho2, 1.0f), 1e-30f)), sh.half != 0,
+                    add_in(true, sqrtf(fmaxf(__fmaf_rn(-d2, irho2, 1.0f), 1e-30f)), LAW != 0 && sh.half != 0,
                            spot_factor(aidx, dw, eb, ii, l0 + k));
                   }
                 }
@@ -2113,15 +2134,20 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
             (void)l;
           };
           // two columns (l, l + 1) with paired operations (binary lens); the
-          // pair row t4 = (x_l, x_l+1, y_l, y_l+1)
-          auto col2 = [&](const float4 t4, bool& unc) {
+          // pair row t4 = (x_l, x_l+1, y_l, y_l+1); hh: std::true_type adds the
+          // half-integer powers s (c1h + c3h mu), s = mu^(1/2) (no spot)
+          auto col2 = [&](const float4 t4, bool& unc, auto hh) {
             const float2 d2 = ray_eval2(ap, make_float2(t4.x, t4.y), make_float2(t4.z, t4.w), ri2, dri2);
             const bool in0 = d2.x < lo2g, in1 = d2.y < lo2g;
             unc = unc || !(in0 || d2.x > hi2g) || !(in1 || d2.y > hi2g);
             win = (win << 2) | (in0 ? 2u : 0u) | (in1 ? 1u : 0u);
             const float2 x = __ffma2_rn(make_float2(-d2.x, -d2.y), irho22, one2);
             const float2 mu = __fmul2_rn(x, make_float2(rsqrt_fast(x.x), rsqrt_fast(x.y)));
-            const float2 J = __fmul2_rn(mu, __ffma2_rn(c2f2, mu, c1f2));
+            float2 J = __fmul2_rn(mu, __ffma2_rn(c2f2, mu, c1f2));
+            if constexpr (decltype(hh)::value) {
+              const float2 sq = __fmul2_rn(mu, make_float2(rsqrt_fast(mu.x), rsqrt_fast(mu.y)));
+              J = __ffma2_rn(sq, __ffma2_rn(c3h2, mu, c1h2), J);
+            }
             sj2 = __fadd2_rn(sj2, make_float2(in0 ? J.x : 0.0f, in1 ? J.y : 0.0f));
           };
           int l = c0;
@@ -2146,21 +2172,24 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                 for (int k = 0; k < KB; k += 2) {
                   const float4 t4 = *reinterpret_cast<const float4*>(tpf + 2 * (l + k));
                   if constexpr (NL == 2) {
-                    col2(t4, unc);
+                    col2(t4, unc, hc);
                   } else {
                     col(l + k, t4.x, t4.z, unc, hc);
                     col(l + k + 1, t4.y, t4.w, unc, hc);
                   }
                 }
               };
-              // (the generic law, half-integer powers or a spot: the scalar loop)
-              if (nb == KB && !sh.generic) {
+              // (a spot, or the half-integer powers outside the generic
+              // instantiation's paired sweep: the scalar loop)
+              if (nb == KB && (LAW == 0 || !sh.generic)) {
                 full_block(std::false_type{});
+              } else if (LAW == 1 && NL == 2 && nb == KB && !sh.spot) {
+                full_block(std::true_type{});
               } else {
 #pragma unroll 1
                 for (int k = 0; k < nb; ++k) {
                   const cf t = tab_at(l + k - gbase);
-                  if (sh.generic) col(l + k, t.x, t.y, unc, std::true_type{});
+                  if (LAW != 0 && sh.generic) col(l + k, t.x, t.y, unc, std::true_type{});
                   else col(l + k, t.x, t.y, unc, std::false_type{});
                 }
               }
@@ -2311,7 +2340,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               }
               if (signbit(sv[2])) {
                 float Id, Ir, Iu;
-                float I = sh.generic ? brightness_der(-sv[2], &Id, &Ir, &Iu, std::true_type{})
+                float I = (LAW != 0 && sh.generic) ? brightness_der(-sv[2], &Id, &Ir, &Iu, std::true_type{})
                                      : brightness_der(-sv[2], &Id, &Ir, &Iu, std::false_type{});
                 // a spot scales the point's brightness and its derivatives
                 I *= fsc; Id *= fsc; Ir *= fsc; Iu *= fsc;
@@ -2425,7 +2454,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
                     const bool in = decide(d2, eb, ii, l0 + k);
                     if (in) win |= 1u << (nb - 1 - k);
                     const float fs = in ? spot_factor(aiD, dw, eb, ii, l0 + k) : 1.f;
-                    const float a = sh.generic ? seed_of(in, d2, pg, rowacc, std::true_type{}, fs)
+                    const float a = (LAW != 0 && sh.generic) ? seed_of(in, d2, pg, rowacc, std::true_type{}, fs)
                                                : seed_of(in, d2, pg, rowacc, std::false_type{}, fs);
                     if (a != 0.f) grad_core(dz, dw, t.x, t.y, ri, (float)(l0 + k) + 0.5f, A01, cs, a, pg);
                   }
@@ -2448,7 +2477,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
               while (l < lend) {
                 const int nb = min(KB, lend - l);
                 bool unc = false;
-                if (sh.generic) {
+                if (LAW != 0 && sh.generic) {
 #pragma unroll 1
                   for (int k = 0; k < nb; ++k) colD(l + k, tab_at(l + k - gbase), unc, std::true_type{});
                 } else {
@@ -2502,7 +2531,7 @@ mag_kernel(const icrs_params* __restrict__ P, int S, const double* __restrict__ 
       // unlensed flux 1 - c F_spot (N = spot_norm); an invalid spot gives NaN
       const double A0 = tot / (sh.rho * sh.rho);
       double A = A0 * sh.spot_norm;
-      if (sh.spot_bad) A = __longlong_as_double(0x7ff8000000000000LL);
+      if (LAW != 0 && sh.spot_bad) A = __longlong_as_double(0x7ff8000000000000LL);
       if (!(A == A) || isinf(A)) sh.status |= ICRS_ST_NAN;
       size_t o = (size_t)s * E + e;
       if (DER) {
@@ -2696,16 +2725,16 @@ static int first_n_lens(const icrs_params* p, cudaStream_t st, int* nl) {
 // Launch of one instantiation at NTB threads per block, with its shared
 // memory, point-table size and flags already chosen: occupancy, contiguous
 // chunks of epochs per block (warm starts along the light curve).
-template <int NL, bool DER, int NTB>
+template <int NL, bool DER, int NTB, int LAW>
 static int launch_nt(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, double* A,
                      uint32_t* status, double* dsect, int32_t* dcnt, float* dpts, const DerOut& dout,
                      cudaStream_t st, const int32_t* items, int n_items, int nsm, size_t smem, int pmax,
                      int has_plo, int defer) {
-  if (cudaFuncSetAttribute(mag_kernel<NL, DER, NTB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+  if (cudaFuncSetAttribute(mag_kernel<NL, DER, NTB, LAW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return ICRS_ECUDA;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mag_kernel<NL, DER, NTB>, NTB, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mag_kernel<NL, DER, NTB, LAW>, NTB, smem) != cudaSuccess)
     return ICRS_ECUDA;
   if (per_sm < 1) return ICRS_EUNSUPPORTED;
   long long tiles = items ? (long long)n_items : (long long)S * E;
@@ -2713,9 +2742,9 @@ static int launch_nt(const icrs_params* p, int S, const double* t, int E, const 
   long long per_block = (tiles + slots - 1) / slots;
   if (per_block < 1) per_block = 1;
   long long blocks = (tiles + per_block - 1) / per_block;
-  mag_kernel<NL, DER, NTB><<<(unsigned)blocks, NTB, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status, dsect,
-                                                                 dcnt, dpts, pmax, has_plo, dout, items, n_items,
-                                                                 defer);
+  mag_kernel<NL, DER, NTB, LAW><<<(unsigned)blocks, NTB, smem, st>>>(p, S, t, E, *g, (int)per_block, A, status,
+                                                                      dsect, dcnt, dpts, pmax, has_plo, dout, items,
+                                                                      n_items, defer);
   return cudaGetLastError() == cudaSuccess ? ICRS_OK : ICRS_ECUDA;
 }
 
@@ -2725,7 +2754,7 @@ static int launch_nt(const icrs_params* p, int S, const double* t, int E, const 
 // the FP64 point table grows (up to one entry per image-limb slot) before
 // the lo parts of image positions are added; derivative mode takes the lo
 // parts first (fewer FP64 polishes).
-template <int NL, bool DER>
+template <int NL, bool DER, int LAW>
 static int launch_inst(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, double* A,
                        uint32_t* status, double* dsect, int32_t* dcnt, float* dpts, const DerOut& dout,
                        cudaStream_t st, const int32_t* items = nullptr, int n_items = 0) {
@@ -2762,11 +2791,22 @@ static int launch_inst(const icrs_params* p, int S, const double* t, int E, cons
   const size_t smem = mag_smem_bytes(NL, *g, pmax, has_plo, DER, defer, nt);
   if constexpr (mag_threads(NL, DER) != NT_BASE) {
     if (nt == mag_threads(NL, DER))
-      return launch_nt<NL, DER, mag_threads(NL, DER)>(p, S, t, E, g, A, status, dsect, dcnt, dpts, dout, st, items,
-                                                      n_items, nsm, smem, pmax, has_plo, defer);
+      return launch_nt<NL, DER, mag_threads(NL, DER), LAW>(p, S, t, E, g, A, status, dsect, dcnt, dpts, dout, st,
+                                                           items, n_items, nsm, smem, pmax, has_plo, defer);
   }
-  return launch_nt<NL, DER, NT_BASE>(p, S, t, E, g, A, status, dsect, dcnt, dpts, dout, st, items, n_items, nsm,
-                                     smem, pmax, has_plo, defer);
+  return launch_nt<NL, DER, NT_BASE, LAW>(p, S, t, E, g, A, status, dsect, dcnt, dpts, dout, st, items, n_items, nsm,
+                                          smem, pmax, has_plo, defer);
+}
+
+// Binary forward: the linear instantiation, then the generic one (each takes
+// its own sets and skips the others; same stream, so they run in order).
+static int launch_binary_fwd(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g, double* A,
+                             uint32_t* status, double* dsect, int32_t* dcnt, float* dpts, cudaStream_t st,
+                             const int32_t* items = nullptr, int n_items = 0) {
+  DerOut none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int rc = launch_inst<2, false, 0>(p, S, t, E, g, A, status, dsect, dcnt, dpts, none, st, items, n_items);
+  if (rc) return rc;
+  return launch_inst<2, false, 1>(p, S, t, E, g, A, status, dsect, dcnt, dpts, none, st, items, n_items);
 }
 
 static int launch_mag(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g,
@@ -2781,8 +2821,8 @@ static int launch_mag(const icrs_params* p, int S, const double* t, int E, const
   if (nl == 0) { rc = first_n_lens(p, st, &nl); if (rc) return rc; }
   if (nl != 2 && nl != 3) return ICRS_EINVAL;
   DerOut none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  if (nl == 2) return launch_inst<2, false>(p, S, t, E, g, A, status, dsect, dcnt, dpts, none, st);
-  return launch_inst<3, false>(p, S, t, E, g, A, status, dsect, dcnt, dpts, none, st);
+  if (nl == 2) return launch_binary_fwd(p, S, t, E, g, A, status, dsect, dcnt, dpts, st);
+  return launch_inst<3, false, 2>(p, S, t, E, g, A, status, dsect, dcnt, dpts, none, st);
 }
 
 // Derivative launch (binary lens only): zeroes the accumulated outputs on the
@@ -2803,7 +2843,7 @@ static int launch_der(const icrs_params* p, int S, const double* t, int E, const
   if (nl == 0) { rc = first_n_lens(p, st, &nl); if (rc) return rc; }
   if (nl == 3 || g->ld_split) return ICRS_EUNSUPPORTED;
   if (nl != 2) return ICRS_EINVAL;
-  return launch_inst<2, true>(p, S, t, E, g, A, status, nullptr, nullptr, nullptr, d, st);
+  return launch_inst<2, true, 2>(p, S, t, E, g, A, status, nullptr, nullptr, nullptr, d, st);
 }
 
 }  // namespace icrs
@@ -2909,8 +2949,8 @@ int icrs_magnification_indexed(const icrs_params* p, int S, const double* t, int
   if (nl == 0) { rc = first_n_lens(p, st, &nl); if (rc) return rc; }
   if (nl != 2 && nl != 3) return ICRS_EINVAL;
   DerOut none = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  if (nl == 2) return launch_inst<2, false>(p, S, t, E, g, A, status, nullptr, nullptr, nullptr, none, st, items, n);
-  return launch_inst<3, false>(p, S, t, E, g, A, status, nullptr, nullptr, nullptr, none, st, items, n);
+  if (nl == 2) return launch_binary_fwd(p, S, t, E, g, A, status, nullptr, nullptr, nullptr, st, items, n);
+  return launch_inst<3, false, 2>(p, S, t, E, g, A, status, nullptr, nullptr, nullptr, none, st, items, n);
 }
 
 int icrs_magnification_vjp(const icrs_params* p, int S, const double* t, int E, const icrs_grid* g,

@@ -44,6 +44,18 @@ def caustic_crossing_binary(n_epochs: int = 500):
     return [p], t[None, :]
 
 
+# Source laws applied on top of a workload's sets (bench.py --law,
+# profile_case laws): the sets' own linear law, a quadratic term, the
+# four-coefficient power series in mu^(1/2) in place of u1, or a dark
+# circular spot (centre (0.3, -0.2) rho, radius 0.4 rho, contrast 0.5).
+SOURCE_LAWS = {
+    "linear": {},
+    "quadratic": dict(u2=0.2),
+    "power4": dict(u1=0.0, a1=0.6, a2=0.3, a3=-0.2, a4=0.1),
+    "spot": dict(spot_x=0.3, spot_y=-0.2, spot_r=0.4, spot_c=0.5),
+}
+
+
 def binary_batch(n_sets: int = 64, n_epochs: int = 10_000, seed: int = 2):
     """log10 q ~ U[-5,-1], s log-uniform [0.3, 3], rho log-uniform [1e-4, 1e-2],
     u0 ~ U[-0.1, 0.1], alpha ~ U[0, 2 pi), u ~ U[0.3, 0.8], tE = 20 d, t0 = 0;

@@ -3,6 +3,7 @@
     python -m paper_2510_02639_gb300.profile_case mag --n-r 1024 --n-theta 2048
     python -m paper_2510_02639_gb300.profile_case der
     python -m paper_2510_02639_gb300.profile_case diag
+    python -m paper_2510_02639_gb300.profile_case laws --sets-stride 1 --epochs-stride 10
     python -m paper_2510_02639_gb300.profile_case mlp_infer --queries 1048576
     python -m paper_2510_02639_gb300.profile_case mlp_train --queries 65536
 
@@ -10,7 +11,10 @@ mag / der: one icrs_magnification / icrs_chi2_grad launch on a strided slice
 of the 64-set binary batch (every --sets-stride-th set, every
 --epochs-stride-th epoch).  diag: the same slice through
 icrs_magnification_diag; prints the clock share of the root and sector
-phases against the ray phase, and the counts of FP64 fallbacks.  mlp_infer / mlp_train: one inference launch or
+phases against the ray phase, and the counts of FP64 fallbacks.  laws: the
+mag launch on the same slice for the sets' linear law and for the same sets
+with inputs.SOURCE_LAWS' power4 and spot laws, each event-timed after one
+untimed launch.  mlp_infer / mlp_train: one inference launch or
 one training step of the surrogate on synthetic features.  Each case runs its
 launch once untimed and once more, so a profiler can skip the first
 (`-s 1` style filters) or take both.
@@ -24,7 +28,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["mag", "der", "diag", "mlp_infer", "mlp_train"])
+    ap.add_argument("case", choices=["mag", "der", "diag", "laws", "mlp_infer", "mlp_train"])
     ap.add_argument("--n-r", type=int, default=1024)
     ap.add_argument("--n-theta", type=int, default=2048)
     ap.add_argument("--sets-stride", type=int, default=2)
@@ -57,6 +61,24 @@ def main(argv=None):
               f"ray phase {rays} ({100 * rays / max(root + rays, 1):.1f}%)")
         print(f"  FP64 polishes {c[0]}, FP64 validations {c[1]}, FP64 rays {c[2]} ({c[2] / max(nray, 1):.2e} of rays), "
               f"FP64 crossings {c[3]}")
+        return
+    if args.case == "laws":
+        params, t = I.binary_batch()
+        sel = list(range(0, len(params), args.sets_stride))
+        tt = torch.tensor(np.ascontiguousarray(t[sel][:, :: args.epochs_stride]), device="cuda")
+        g = icrs.grid_from_dict(I.grid(n_r=args.n_r, n_theta=args.n_theta), 2)
+        for name in ("linear", "power4", "spot"):
+            pd = icrs.params_to_device([dict(params[s], **I.SOURCE_LAWS[name]) for s in sel])
+            A, st = icrs.magnification(pd, tt, g)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            icrs.magnification(pd, tt, g, out=A, status=st)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            print(f"laws: {name}: {tt.numel()} epochs at {args.n_r}x{args.n_theta}, {ms:.1f} ms, "
+                  f"{tt.numel() / ms * 1e3:.0f} magnifications/s, finite {bool(torch.isfinite(A).all())}")
         return
     if args.case in ("mag", "der"):
         params, t = I.binary_batch()

@@ -253,8 +253,9 @@ def test_quadratic_limb_darkening_and_split_rule(G, oracle_mod):
 @pytest.mark.parametrize("coef", [(0.6, 0.0, 0.0, 0.0), (0.3, 0.2, -0.1, 0.05), (0.0, 0.3, 0.0, 0.2)])
 def test_power_series_profiles(G, oracle_mod, coef):
     """The power-series law in mu^(1/2) (coefficients a1..a4 on top of u1 =
-    0.2; half-integer powers take the kernel's second sweep variant, integer
-    ones the default) on the caustic-crossing curve and on 64 batch epochs,
+    0.2; half-integer powers take the kernel's generic instantiation and its
+    paired half-power sweep, integer ones the linear instantiation) on the
+    caustic-crossing curve and on 64 batch epochs,
     with the literal and the split-profile rules: against the oracle at 1e-5
     with the same status bits."""
     a = dict(a1=coef[0], a2=coef[1], a3=coef[2], a4=coef[3])
