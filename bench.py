@@ -663,7 +663,9 @@ def main():
         "marginal_nll_grad": nll,
         "surrogate": sur,
         "clocks": clocks,
-        "gpu_launches": args.steps,
+        # binary: the linear and the generic instantiation of the forward
+        # kernel per step (each skips the other's sets); triple: one
+        "gpu_launches": args.steps * (2 if n_lens == 2 else 1),
         "status_flags": {k: int(np.count_nonzero(stc & b)) for k, b in
                          [("nonconv", 1), ("imgcount", 2), ("sectcap", 4), ("edge", 8), ("nan", 16), ("overflow", 32)]},
         "wall_s": wall,
