@@ -653,7 +653,8 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "note": f"ray-stage algorithmic FP32 flops ({FLOPS_PER_RAY[n_lens]:.0f}/ray, {rays:.3e} rays/step) "
-                             f"over the fused kernel's event time; peak = 152 SM x 128 FP32 lanes x 2 x max SM clock "
+                             f"over the step's event time (binary: the linear instantiation does the work, the generic one skips "
+                             f"every set of a linear batch); peak = 152 SM x 128 FP32 lanes x 2 x max SM clock "
                              f"(derived, no measured FP32 entry)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
