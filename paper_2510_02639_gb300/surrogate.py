@@ -213,6 +213,13 @@ def calibrate(sur: Surrogate, val: Dataset, tol: float = 1e-4, margin: float = 2
     return Gate(smax, mu_max, b_max, caustic_min, A_max, rho_min, A_small)
 
 
+def _clean_without_network(st):
+    """Feature status that lets the non-learned rules (icrs_epoch_gate)
+    accept an epoch: clean apart from ICRS_ST_PROFILE, since the second-order
+    estimate uses each radial law's own second moment."""
+    return (st & ~icrs.ST_PROFILE) == 0
+
+
 def calibrate_point_source(val: Dataset, tol: float = 1e-4, margin: float = 2.0, use_estimate: bool = False,
                            exceed_frac: float = EXCEED_FRAC):
     """The method without the network: A = A_ps (use_estimate: A = A_ps
@@ -224,7 +231,7 @@ def calibrate_point_source(val: Dataset, tol: float = 1e-4, margin: float = 2.0,
     Aest = val.A_ps * torch.exp(val.feat[:, 7].double() / icrs.TARGET_SCALE) if use_estimate else val.A_ps
     err = (Aest / val.A - 1.0).abs()
     c = val.feat[:, 6].double()
-    ok = val.st == 0
+    ok = _clean_without_network(val.st)
     order = torch.argsort(c, descending=True)
     last = _loosest_prefix(ok[order], err[order], tol / margin, exceed_frac)
     return float(c[order][last].item()) if last >= 0 else 2.0
@@ -244,7 +251,7 @@ def calibrate_estimate(val: Dataset, tol: float = 1e-4, margin: float = 2.0,
     best, best_n = (2.0, 0.0), -1
     for c in caustic_grid:
         for bm in b_grid:
-            sel = ((val.st == 0) & (val.feat[:, 6] >= c) & (b.abs() <= bm)
+            sel = (_clean_without_network(val.st) & (val.feat[:, 6] >= c) & (b.abs() <= bm)
                    & (val.A_ps <= torch.where(val.feat[:, 4] >= float(np.log10(rho_min)) + 3.0, A_max, A_small)))
             n = int(sel.sum().item())
             n_bad = int((err[sel] > tol / margin).sum().item())

@@ -57,3 +57,32 @@ def test_calibrate_tolerates_rare_label_outliers():
     g1 = SG.calibrate(_FakeSur(sig), val, exceed_frac=1e-4)
     assert abs(g0.sigma_max - 99e-6) < 1e-9
     assert abs(g1.sigma_max - 1e-2) < 1e-8
+
+
+def test_status_rules_of_the_two_gates():
+    """The learned gate's calibration accepts only clean feature status; the
+    non-learned rules (second-order estimate, point source) also accept
+    ICRS_ST_PROFILE, since their estimate uses each radial law's moment, and
+    reject ICRS_ST_SPOT and the solve and roughness bits.  Exact labels, so
+    only the status decides."""
+    from paper_2510_02639_gb300 import icrs
+    bits = [0, icrs.ST_PROFILE, icrs.ST_SPOT, icrs.ST_ROUGH, icrs.ST_LIMB | icrs.ST_PROFILE]
+    n = len(bits)
+    st = torch.tensor(bits, dtype=torch.int32)
+    feat = torch.zeros(n, 8)
+    feat[:, 4] = 3.0  # log10 rho + 3 = 0: rho = 1 (above rho_min)
+    one = torch.ones(n, dtype=torch.float64)
+    val = SG.Dataset(feat=feat, A_ps=one, st=st, A=one.clone(), target=torch.zeros(n), params=None, t=None)
+    assert SG._clean_without_network(st).tolist() == [True, True, False, False, False]
+    # every accepted epoch is exact, so the loosest rule wins: the smallest
+    # caustic threshold and b_max of the grids
+    assert SG.calibrate_estimate(val) == (-6.0, 1.0)
+    g = SG.calibrate(_FakeSur(torch.full((n,), 1e-6, dtype=torch.float64)), val)
+    assert abs(g.sigma_max - 1e-6) < 1e-12
+    # a wrong label under ICRS_ST_PROFILE: every non-learned candidate rule
+    # accepts it and so none qualifies (the (2, 0) sentinel), while the
+    # learned rule never sees it
+    val.A[1] = 2.0
+    assert SG.calibrate_estimate(val, exceed_frac=0.0) == (2.0, 0.0)
+    g = SG.calibrate(_FakeSur(torch.full((n,), 1e-6, dtype=torch.float64)), val, exceed_frac=0.0)
+    assert abs(g.sigma_max - 1e-6) < 1e-12
