@@ -178,7 +178,10 @@ int icrs_point_source(const icrs_params* p, int S, const double* w, int n,
  *   A       [S][E] device double (out)
  *   status  [S][E] device uint32 or NULL (out)
  * One persistent CUDA kernel runs the whole per-epoch path: limb roots,
- * sectors, rays and the brightness reduction.  Errors: ICRS_EINVAL for bad
+ * sectors, rays and the brightness reduction.  A binary lens launches it
+ * twice on the stream: an instantiation for the sets whose law has no
+ * half-integer powers and no spot, then one for the other sets; each skips
+ * the other's sets, so every (set, epoch) is computed once.  Errors: ICRS_EINVAL for bad
  * sizes or grid, ICRS_EUNSUPPORTED if the grid needs more shared memory than
  * an SM has, ICRS_ECUDA on launch failure.
  */
