@@ -167,7 +167,9 @@ def brute_force_magnification(eps, a, wc, rho, u1=0.0, uniform=True, h_coarse=4e
     """Inverse-ray shooting on a Cartesian grid (independent of the polar
     sectors): a coarse pass over [-box, box]^2 finds the pixels whose rays land
     within (1 + pad) rho of the source centre; each connected bounding box is
-    then sampled at pixel size rho / refine.  Surface brightness: uniform (1/pi)
+    then sampled at pixel size rho / refine, skipping the points that an
+    earlier box already holds (the box of a ring-shaped image can contain
+    the boxes of other images).  Surface brightness: uniform (1/pi)
     or linear limb darkening, times weight((w - w_c) / rho) if given (not
     renormalised); A = sum I h^2 / rho^2."""
     xs = np.arange(-box, box, h_coarse) + 0.5 * h_coarse
@@ -181,6 +183,7 @@ def brute_force_magnification(eps, a, wc, rho, u1=0.0, uniform=True, h_coarse=4e
     total = 0.0
     h = rho / refine
     I0 = 3.0 / (np.pi * (3.0 - u1))
+    done = []  # boxes already sampled: (x0, x1, y0, y1)
     for obj in ndimage.find_objects(lab):
         xi, yi = obj
         x0, x1 = xs[xi.start] - 2 * h_coarse, xs[xi.stop - 1] + 2 * h_coarse
@@ -192,6 +195,8 @@ def brute_force_magnification(eps, a, wc, rho, u1=0.0, uniform=True, h_coarse=4e
             wn = (lens_map(eps, a, FX + 1j * FY) - wc) / rho
             dd = np.abs(wn)
             inside = dd < 1.0
+            for bx0, bx1, by0, by1 in done:
+                inside &= ~((FX >= bx0) & (FX < bx1) & (FY >= by0) & (FY < by1))
             if uniform:
                 I = np.full(dd.shape, 1.0 / np.pi)
             else:
@@ -200,4 +205,5 @@ def brute_force_magnification(eps, a, wc, rho, u1=0.0, uniform=True, h_coarse=4e
             if weight is not None:
                 I = I * weight(wn)
             total += np.sum(I[inside])
+        done.append((fx[0] - 0.5 * h, fx[-1] + 0.5 * h, fy[0] - 0.5 * h, fy[-1] + 0.5 * h))
     return total * h * h / (rho * rho)

@@ -255,6 +255,31 @@ def test_brute_force_binary(oracle_mod, case):
     assert abs(A[0, 0] / ref - 1.0) < 2e-3, (A, ref)
 
 
+@pytest.mark.parametrize("case", [
+    dict(q2=0.2, q3=0.1, s2=1.0, s3=0.7, psi=1.0, w=0.02 + 0.03j, uniform=1, u1=0.0),
+    dict(q2=0.1, q3=0.05, s2=0.9, s3=0.6, psi=2.2, w=-0.05 + 0.02j, uniform=0, u1=0.5),
+    dict(q2=0.3, q3=0.2, s2=1.2, s3=0.5, psi=0.4, w=0.1 - 0.1j, uniform=0, u1=0.6),
+])
+def test_brute_force_triple(oracle_mod, case):
+    """(d) Triple lens with third masses of 5-20 % (eight or six images, one
+    case at A_ps ~ 135 next to a caustic, one with a ring-shaped image whose
+    box holds the others), rho = 0.05: the oracle agrees with Cartesian
+    inverse-ray shooting to the brute force's pixel error.  A wrong triple
+    polynomial coefficient, a missed image or a sector that clips one would
+    show at the percent level."""
+    rho = 0.05
+    w = case["w"]
+    p = I.triple(q2=case["q2"], q3=case["q3"], s2=case["s2"], s3=case["s3"], psi=case["psi"], rho=rho,
+                 u1=case["u1"], t0=0.0, tE=1.0, u0=w.imag, alpha=0.0)
+    g = I.grid(n_r=200, n_theta=800, uniform=case["uniform"])
+    A, st = oracle_mod.magnification(p, [w.real], g)
+    assert st[0, 0] == 0
+    eps, a = oracle_mod.lens(p)
+    ref = CF.brute_force_magnification(eps, a, w, rho, u1=case["u1"], uniform=bool(case["uniform"]),
+                                       refine=120)
+    assert abs(A[0, 0] / ref - 1.0) < 5e-4, (A, ref)
+
+
 def test_full_disk_spot_leaves_magnification(oracle_mod):
     """A spot covering the whole disk (centre 0, radius 1) scales every ray
     and the unlensed flux alike: the magnification is the unspotted one
