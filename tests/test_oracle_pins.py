@@ -280,6 +280,30 @@ def test_brute_force_triple(oracle_mod, case):
     assert abs(A[0, 0] / ref - 1.0) < 5e-4, (A, ref)
 
 
+@pytest.mark.parametrize("case", [(0.05, 1.3, 0.3 - 0.05j), (1.0, 0.8, 0.05 + 0.04j), (0.2, 1.0, 0.02 + 0.01j)])
+def test_brute_force_power_series_binary(oracle_mod, case):
+    """(d) Binary lens, rho = 0.05, the four-coefficient law in mu^(1/2)
+    (u1 = 0, a = 0.6, 0.3, -0.2, 0.1): the oracle at 200 x 800 agrees with
+    Cartesian inverse-ray shooting whose brightness is the law written out
+    here, I0 [1 - sum_k a_k (1 - mu^(k/2))] with I0 = 1 / (pi (1 - sum_k a_k
+    k/(k+4))), to 5e-4."""
+    q, s, w = case
+    a = (0.6, 0.3, -0.2, 0.1)
+    I0 = 1.0 / (np.pi * (1.0 - sum(a[k - 1] * k / (k + 4.0) for k in range(1, 5))))
+
+    def weight(wn):  # the law over the uniform brute force's 1/pi
+        mu = np.sqrt(1.0 - np.minimum(np.abs(wn) ** 2, 1.0))
+        return np.pi * I0 * (1.0 - sum(a[k - 1] * (1.0 - mu ** (k / 2.0)) for k in range(1, 5)))
+
+    rho = 0.05
+    p = I.binary(q=q, s=s, rho=rho, u1=0.0, t0=0.0, tE=1.0, u0=w.imag, alpha=0.0)
+    p.update(a1=a[0], a2=a[1], a3=a[2], a4=a[3])
+    A, st = oracle_mod.magnification(p, [w.real], I.grid(n_r=200, n_theta=800))
+    eps, al = oracle_mod.lens(p)
+    ref = CF.brute_force_magnification(eps, al, w, rho, uniform=True, refine=120, weight=weight)
+    assert abs(A[0, 0] / ref - 1.0) < 5e-4, (A, ref)
+
+
 def test_full_disk_spot_leaves_magnification(oracle_mod):
     """A spot covering the whole disk (centre 0, radius 1) scales every ray
     and the unlensed flux alike: the magnification is the unspotted one
