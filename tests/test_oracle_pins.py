@@ -492,6 +492,21 @@ def test_forward_mode_matches_fd(oracle_mod):
     assert agreed == compared
 
 
+def test_all_core_build_equals_the_serial_oracle(oracle_mod):
+    """The OpenMP build that times the all-core CPU baseline runs the same
+    source over independent epochs: bitwise the serial build's A and
+    status, including a spotted and a power-series set."""
+    params, t = I.binary_batch()
+    ps = [params[5], dict(params[9], a1=0.3, a3=-0.1),
+          dict(params[13], spot_x=0.2, spot_y=0.1, spot_r=0.3, spot_c=0.4)]
+    tt = np.stack([t[5, 4990:4996], t[9, ::1700][:6], t[13, 5000:5006]])
+    g = I.grid()
+    A1, s1 = oracle_mod.magnification(ps, tt, g)
+    A2, s2 = oracle_mod.magnification_all_cores(ps, tt, g)
+    np.testing.assert_array_equal(A1, A2)
+    np.testing.assert_array_equal(s1, s2)
+
+
 def test_image_tolerance_convention_does_not_change_results(oracle_mod):
     """img_tol is a convention: true images have FP64 residuals ~1e-15 and the
     polynomial's spurious roots residuals ~1e-2 or more, so img_tol = 1e-3
